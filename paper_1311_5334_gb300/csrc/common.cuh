@@ -1,0 +1,157 @@
+// common.cuh -- device-side structures shared by the kernel translation units
+// of libet (grain-pair seeded straight-line track finding, Section 2 of the
+// paper).  Host code sees these through the launcher declarations at the end.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace et {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ---------------------------------------------------------------- error bits
+enum : u32 {
+    ERRB_OUT_OF_RANGE = 1u << 0,
+    ERRB_DUPLICATE = 1u << 1,
+    ERRB_OVF_SEEDS = 1u << 2,
+    ERRB_OVF_CAND = 1u << 3,
+    ERRB_OVF_MEMBERS = 1u << 4,
+    ERRB_TIMEOUT = 1u << 5,
+    ERRB_OVF_RECORD = 1u << 6,
+    ERRB_INPUT_MASK = ERRB_OUT_OF_RANGE | ERRB_DUPLICATE,
+    ERRB_OVF_MASK = ERRB_OVF_SEEDS | ERRB_OVF_CAND | ERRB_OVF_MEMBERS | ERRB_OVF_RECORD,
+};
+
+// Candidate states during the merge.
+enum : unsigned char { CS_UNDECIDED = 0, CS_ACCEPTED = 1, CS_REJECTED = 2 };
+
+// Device control block: counters written by the kernels, read back by the host.
+struct Ctl {
+    u64 n_seeds;        // total seeds (scan result)
+    u64 n_tests;        // tube tests performed
+    u64 n_hits;         // sum of counts over seeds
+    u64 n_cand;         // candidates appended (may exceed capacity -> overflow bit)
+    u64 n_members;      // sum of candidate counts (scan result)
+    u64 n_acc;          // accepted tracks
+    u64 n_out_members;  // members of accepted tracks
+    u64 n_record;       // per-seed records written (diagnostic path)
+    u32 error;          // ERRB_* bits
+    u32 rounds;         // merge rounds run
+    u32 bar_count;      // grid barrier arrivals
+    u32 bar_gen;        // grid barrier generation
+    u32 active[2];      // merge: participants per round (ping-pong)
+    u32 pad[2];
+};
+
+// Everything a kernel needs to know about the batch.  Passed by value.
+struct Batch {
+    int V;               // views
+    int N;               // grains in all views
+    const long long *goff;   // V + 1 grain offsets (device)
+    // parameters
+    int ext[3];
+    int smin, smax, r, H;
+    long long smin2, smax2, r2;
+    // cell grid (identical for all views)
+    int cs[3];           // cell edge per axis
+    int nc[3];           // cells per axis
+    float ics[3];        // 1 / cs
+    int ncell;           // cells per view
+    int cbits[3];        // bit widths of x, y, z in the canonical key
+    int vshift;          // bit position of the view index in the canonical key
+    // arrays
+    const int *xyz_in;   // N x 3 input, caller order
+    int4 *gr;            // canonical order: x, y, z, caller index within the view
+    int4 *gc;            // cell order: x, y, z, canonical (global) index
+    u32 *cell_start;     // V * ncell + 1
+    Ctl *ctl;
+};
+
+// Seeds and candidates.
+struct Work {
+    int2 *seeds;         // (lo, hi) canonical global indices
+    u64 seed_cap;
+    u64 *seed_off;       // per grain (cell order) exclusive offsets, N + 1
+    // candidates
+    int *c_lo, *c_hi;    // canonical global indices
+    u32 *c_cnt;          // tube count
+    u64 *c_key;          // (2^21-1-count) << 42 | rank_lo << 21 | rank_hi
+    u64 *c_moff;         // member offsets, cap + 1
+    unsigned char *c_state;
+    u32 *c_nfree;        // unused grains when accepted
+    u64 cand_cap;
+    int *members;        // canonical global indices
+    u64 member_cap;
+    // merge
+    u64 *best[2];        // per grain
+    int *owner;          // per grain: accepting candidate or -1
+    // diagnostic per-seed record (optional)
+    int *rec_lo, *rec_hi, *rec_cnt;
+    u64 rec_cap;
+};
+
+// Output stage.
+struct Out {
+    int *acc;            // accepted candidate ids, later sorted by (view, key)
+    u64 acc_cap;
+    u64 *sort_k[2];      // scratch keys for sorting the accepted list / members
+    u32 *sort_v[2];
+    int *trk_view;       // view of each accepted track (sorted order)
+    u64 *trk_moff;       // member offsets of accepted tracks (sorted order), cap + 1
+    long long *view_trk; // V + 1 track offsets
+    void *tracks;        // et_track[acc_cap]
+    int *out_members;    // caller indices, sorted within each track
+    u64 out_member_cap;
+};
+
+__device__ __forceinline__ int view_of(const long long *goff, int V, long long g) {
+    int lo = 0, hi = V - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (goff[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool input_failed(const Ctl *ctl) {
+    return (*(volatile const u32 *)&ctl->error & (ERRB_INPUT_MASK | ERRB_OVF_MASK | ERRB_TIMEOUT)) != 0;
+}
+
+// ---------------------------------------------------------------- launchers
+// scan_sort.cu
+size_t radix_temp_bytes(long long n);
+// Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key.
+// Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
+// (k0, v0), 1 if in (k1, v1).
+int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp,
+                     cudaStream_t st);
+size_t scan_temp_bytes(long long n);
+// Exclusive prefix sum of n values; writes n + 1 outputs (the last = total).
+// If total_out != nullptr the total is also stored there.  In place allowed.
+void exclusive_scan_u64(const u64 *in, u64 *out, long long n, void *temp, u64 *total_out,
+                        cudaStream_t st);
+void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaStream_t st);
+// Same over [0, min(*n_dev, n_cap)) when n_dev is not null.
+void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
+                            u64 *total_out, cudaStream_t st);
+int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,
+                         void *temp, cudaStream_t st);
+
+// grid.cu
+void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st);
+void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u64 *ckeys, u32 *cvals,
+                            u32 *cell_count, cudaStream_t st);
+void launch_cell_order(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
+
+// count.cu
+void launch_seed_count(const Batch &b, const Work &w, cudaStream_t st);
+void launch_seed_fill(const Batch &b, const Work &w, cudaStream_t st);
+void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st);
+void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st);
+void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st);
+
+// merge.cu
+int merge_grid_blocks(int device);
+
+}  // namespace et

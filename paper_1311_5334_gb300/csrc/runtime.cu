@@ -1,0 +1,807 @@
+// runtime.cu -- host runtime behind the C ABI of include/et.h: contexts,
+// batches (a view is a batch of one), device buffers with capacity growth,
+// the launch sequence of the hot path and its CUDA-graph replay.
+#include "runtime.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+namespace et {
+
+cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStream_t st);
+void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, long long out_member_cap,
+                   void *temp, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+et_status fail(et_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+et_status cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(ET_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(ET_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+int bits_for(unsigned long long maxval) {
+    int b = 0;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- context
+
+void *Ctx::dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (alloc) return alloc(bytes, user);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void Ctx::dfree(void *p) {
+    if (!p) return;
+    if (free_fn) free_fn(p, user);
+    else cudaFree(p);
+}
+
+// ---------------------------------------------------------------- groups
+
+bool Group::reserve(Ctx *ctx, size_t need) {
+    if (need <= bytes && base) return true;
+    release(ctx);
+    base = (char *)ctx->dalloc(need);
+    if (!base) return false;
+    bytes = need;
+    ++generation;
+    return true;
+}
+
+void Group::release(Ctx *ctx) {
+    if (base) ctx->dfree(base);
+    base = nullptr;
+    bytes = 0;
+}
+
+// Carves consecutive 256-byte aligned slices out of one allocation.
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count) {
+        size_t o = off;
+        off = align_up(off + count * sizeof(T), 256);
+        return base ? (T *)(base + o) : nullptr;
+    }
+};
+
+// ---------------------------------------------------------------- parameters
+
+et_status check_params(const et_params *p) {
+    if (!p) return fail(ET_ERR_INVALID_ARG, "params is NULL");
+    for (int k = 0; k < 3; ++k)
+        if (p->extent[k] <= 0 || p->extent[k] > (1 << 21))
+            return fail(ET_ERR_INVALID_ARG, "extent[%d] = %d outside (0, 2^21]", k, p->extent[k]);
+    if (p->seed_max < 1 || p->seed_min < 0 || p->seed_min > p->seed_max)
+        return fail(ET_ERR_INVALID_ARG, "seed window [%d, %d) invalid", p->seed_min, p->seed_max);
+    if (p->tube_r < 0 || p->tube_r > (1 << 20)) return fail(ET_ERR_INVALID_ARG, "tube_r = %d", p->tube_r);
+    if (p->min_hits < 1) return fail(ET_ERR_INVALID_ARG, "min_hits = %d < 1", p->min_hits);
+    if (p->flags != 0) return fail(ET_ERR_INVALID_ARG, "flags = %u: no variant is defined", p->flags);
+    for (int a = 0; a < 3; ++a)
+        for (int c = a + 1; c < 3; ++c) {
+            long long v = ((long long)p->extent[a] + p->extent[c]) * (long long)p->seed_max;
+            if (v >= (1ll << 31))
+                return fail(ET_ERR_PRECONDITION,
+                            "(extent[%d] + extent[%d]) * seed_max = %lld >= 2^31: cross products leave int32", a,
+                            c, v);
+        }
+    return ET_OK;
+}
+
+// ---------------------------------------------------------------- batch
+
+BatchRT::BatchRT(Ctx *c, const et_params &pp) : ctx(c), p(pp) {
+    memset(&tune, 0, sizeof tune);
+    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+}
+
+BatchRT::~BatchRT() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (done) cudaEventDestroy(done);
+    for (Group *g : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
+        g->release(ctx);
+}
+
+void BatchRT::choose_cells() {
+    for (int k = 0; k < 3; ++k) cs[k] = tune.cell[k];
+    if (cs[0] <= 0 || cs[1] <= 0 || cs[2] <= 0) {
+        // grains per cell ~ 0.35 at the mean density of the batch
+        double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
+        double nmean = V > 0 ? (double)N / V : 1.0;
+        double rho = std::max(nmean, 1.0) / vol;
+        double s = std::cbrt(0.35 / rho);
+        s = std::min(std::max(s, 64.0), 4096.0);
+        for (int k = 0; k < 3; ++k)
+            if (tune.cell[k] <= 0) cs[k] = (int)std::lround(s);
+    }
+    for (int k = 0; k < 3; ++k) {
+        cs[k] = std::max(1, std::min(cs[k], p.extent[k]));
+        nc[k] = (p.extent[k] + cs[k] - 1) / cs[k];
+    }
+    ncell = (long long)nc[0] * nc[1] * nc[2];
+}
+
+void BatchRT::estimate_caps() {
+    const double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
+    const double shell = 4.0 / 3.0 * M_PI *
+                         (std::pow((double)p.seed_max, 3) - std::pow((double)p.seed_min, 3));
+    const double frac = std::min(1.0, shell / vol);
+    double s = 0;
+    for (int v = 0; v < V; ++v) {
+        double n = (double)(goff_h[v + 1] - goff_h[v]);
+        s += 0.5 * n * n * frac;
+    }
+    u64 seeds = (u64)(1.3 * s) + 4096;
+    want_seeds = std::max(want_seeds, seeds);
+    want_cand = std::max(want_cand, std::max<u64>(65536, seeds / 16));
+    want_members = std::max(want_members, want_cand * 24);
+}
+
+et_status BatchRT::reserve() {
+    // small: control block, goff, per-view track offsets
+    {
+        Carver cv;
+        cv.take<Ctl>(1);
+        cv.take<long long>(V + 1);
+        cv.take<long long>(V + 1);
+        if (!g_small.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "control block");
+        Carver c2{0, g_small.base};
+        ctl = c2.take<Ctl>(1);
+        goff = c2.take<long long>(V + 1);
+        view_trk = c2.take<long long>(V + 1);
+    }
+    const size_t n = (size_t)std::max<long long>(N, 1);
+    {
+        Carver cv;
+        auto lay = [&](Carver &c) {
+            xyz_in = c.take<int>(3 * n);
+            keys[0] = c.take<u64>(n);
+            keys[1] = c.take<u64>(n);
+            vals[0] = c.take<u32>(n);
+            vals[1] = c.take<u32>(n);
+            gr = c.take<int4>(n);
+            gc = c.take<int4>(n);
+            seed_off = c.take<u64>(n + 1);
+            best[0] = c.take<u64>(n);
+            best[1] = c.take<u64>(n);
+            owner = c.take<int>(n);
+        };
+        lay(cv);
+        if (!g_grain.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "grain buffers (%zu bytes)", cv.off);
+        Carver c2{0, g_grain.base};
+        lay(c2);
+    }
+    const size_t cells = (size_t)V * (size_t)ncell;
+    {
+        Carver cv;
+        cv.take<u32>(cells);
+        cv.take<u32>(cells + 1);
+        if (!g_cells.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "cell table (%zu bytes)", cv.off);
+        Carver c2{0, g_cells.base};
+        cell_count = c2.take<u32>(cells);
+        cell_start = c2.take<u32>(cells + 1);
+    }
+    {
+        size_t need = want_seeds * sizeof(int2);
+        if (!g_seeds.reserve(ctx, align_up(need, 256))) return fail(ET_ERR_OOM, "seeds (%zu bytes)", need);
+        seeds = (int2 *)g_seeds.base;
+        cap_seeds = g_seeds.bytes / sizeof(int2);
+    }
+    {
+        const size_t cc = want_cand;
+        auto lay = [&](Carver &c) {
+            c_lo = c.take<int>(cc);
+            c_hi = c.take<int>(cc);
+            c_cnt = c.take<u32>(cc);
+            c_key = c.take<u64>(cc);
+            c_moff = c.take<u64>(cc + 1);
+            c_state = c.take<unsigned char>(cc);
+            c_nfree = c.take<u32>(cc);
+        };
+        Carver cv;
+        lay(cv);
+        if (!g_cand.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "candidates (%zu bytes)", cv.off);
+        Carver c2{0, g_cand.base};
+        lay(c2);
+        cap_cand = cc;
+    }
+    {
+        size_t need = want_members * sizeof(int);
+        if (!g_members.reserve(ctx, align_up(need, 256))) return fail(ET_ERR_OOM, "members (%zu bytes)", need);
+        members = (int *)g_members.base;
+        cap_members = g_members.bytes / sizeof(int);
+    }
+    {
+        const size_t cc = cap_cand, sk = std::max<size_t>(cc, n);
+        auto lay = [&](Carver &c) {
+            acc = c.take<int>(cc);
+            sort_k[0] = c.take<u64>(sk);
+            sort_k[1] = c.take<u64>(sk);
+            sort_v[0] = c.take<u32>(sk);
+            sort_v[1] = c.take<u32>(sk);
+            trk_view = c.take<int>(cc);
+            trk_moff = c.take<u64>(cc + 1);
+            tracks = c.take<et_track>(cc);
+            out_members = c.take<int>(n);
+        };
+        Carver cv;
+        lay(cv);
+        if (!g_out.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "outputs (%zu bytes)", cv.off);
+        Carver c2{0, g_out.base};
+        lay(c2);
+    }
+    if (want_rec) {
+        Carver cv;
+        cv.take<int>(want_rec);
+        cv.take<int>(want_rec);
+        cv.take<int>(want_rec);
+        if (!g_rec.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "seed records (%zu bytes)", cv.off);
+        Carver c2{0, g_rec.base};
+        rec_lo = c2.take<int>(want_rec);
+        rec_hi = c2.take<int>(want_rec);
+        rec_cnt = c2.take<int>(want_rec);
+        cap_rec = want_rec;
+    }
+    {
+        size_t t = 0;
+        t = std::max(t, radix_temp_bytes((long long)n));
+        t = std::max(t, radix_temp_bytes((long long)std::max<size_t>(cap_cand, n)));
+        t = std::max(t, scan_temp_bytes((long long)cells + 1));
+        t = std::max(t, scan_temp_bytes((long long)n + 1));
+        t = std::max(t, scan_temp_bytes((long long)cap_cand + 1));
+        t = std::max(t, scan_temp_bytes((long long)V + 1));
+        if (!g_temp.reserve(ctx, align_up(t, 256))) return fail(ET_ERR_OOM, "temp (%zu bytes)", t);
+        temp = g_temp.base;
+    }
+    return ET_OK;
+}
+
+unsigned long long BatchRT::layout_generation() const {
+    unsigned long long g = 0;
+    for (const Group *x : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
+        g = g * 1315423911ull + x->generation;
+    return g;
+}
+
+et_status BatchRT::load(const int32_t *xyz, const int64_t *offsets, int nv, bool on_device, cudaStream_t st) {
+    if (nv < 0 || !offsets) return fail(ET_ERR_INVALID_ARG, "bad view list");
+    if (offsets[0] != 0) return fail(ET_ERR_INVALID_ARG, "offsets[0] must be 0");
+    long long mx = 0;
+    for (int v = 0; v < nv; ++v) {
+        long long n = offsets[v + 1] - offsets[v];
+        if (n < 0) return fail(ET_ERR_INVALID_ARG, "offsets must be non-decreasing");
+        if (n > (1 << 21) - 1) return fail(ET_ERR_INVALID_ARG, "view %d has %lld grains (max 2^21-1)", v, n);
+        mx = std::max(mx, n);
+    }
+    const long long total = offsets[nv];
+    if (total > 0 && !xyz) return fail(ET_ERR_INVALID_ARG, "xyz is NULL");
+    if (total >= (1ll << 31) - 1) return fail(ET_ERR_INVALID_ARG, "batch of %lld grains too large", total);
+    // canonical key: view | x | y | z
+    int cb[3];
+    for (int k = 0; k < 3; ++k) cb[k] = bits_for((unsigned long long)(p.extent[k] - 1));
+    int vb = bits_for((unsigned long long)std::max(nv - 1, 0));
+    if (cb[0] + cb[1] + cb[2] + vb > 64) return fail(ET_ERR_INVALID_ARG, "too many views for the key width");
+    V = nv;
+    N = total;
+    maxN = mx;
+    goff_h.assign(offsets, offsets + nv + 1);
+    for (int k = 0; k < 3; ++k) cbits[k] = cb[k];
+    choose_cells();
+    if ((double)V * (double)ncell >= 4.0e9) return fail(ET_ERR_INVALID_ARG, "cell table too large");
+    estimate_caps();
+    et_status s = reserve();
+    if (s != ET_OK) return s;
+    cudaError_t e = cudaMemcpyAsync(goff, goff_h.data(), sizeof(long long) * (V + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && N > 0)
+        e = cudaMemcpyAsync(xyz_in, xyz, sizeof(int) * 3 * (size_t)N,
+                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "grain upload");
+    loaded = true;
+    ran = false;
+    return ET_OK;
+}
+
+Batch BatchRT::dev_batch() const {
+    Batch b;
+    memset(&b, 0, sizeof b);
+    b.V = V;
+    b.N = (int)N;
+    b.goff = goff;
+    for (int k = 0; k < 3; ++k) {
+        b.ext[k] = p.extent[k];
+        b.cs[k] = cs[k];
+        b.nc[k] = nc[k];
+        b.ics[k] = 1.0f / (float)cs[k];
+        b.cbits[k] = cbits[k];
+    }
+    b.smin = p.seed_min;
+    b.smax = p.seed_max;
+    b.r = p.tube_r;
+    b.H = p.min_hits;
+    b.smin2 = (long long)p.seed_min * p.seed_min;
+    b.smax2 = (long long)p.seed_max * p.seed_max;
+    b.r2 = (long long)p.tube_r * p.tube_r;
+    b.ncell = (int)ncell;
+    b.vshift = cbits[0] + cbits[1] + cbits[2];
+    b.xyz_in = xyz_in;
+    b.gr = gr;
+    b.gc = gc;
+    b.cell_start = cell_start;
+    b.ctl = ctl;
+    return b;
+}
+
+Work BatchRT::dev_work() const {
+    Work w;
+    memset(&w, 0, sizeof w);
+    w.seeds = seeds;
+    w.seed_cap = cap_seeds;
+    w.seed_off = seed_off;
+    w.c_lo = c_lo;
+    w.c_hi = c_hi;
+    w.c_cnt = c_cnt;
+    w.c_key = c_key;
+    w.c_moff = c_moff;
+    w.c_state = c_state;
+    w.c_nfree = c_nfree;
+    w.cand_cap = cap_cand;
+    w.members = members;
+    w.member_cap = cap_members;
+    w.best[0] = best[0];
+    w.best[1] = best[1];
+    w.owner = owner;
+    w.rec_lo = rec_lo;
+    w.rec_hi = rec_hi;
+    w.rec_cnt = rec_cnt;
+    w.rec_cap = cap_rec;
+    return w;
+}
+
+Out BatchRT::dev_out() const {
+    Out o;
+    memset(&o, 0, sizeof o);
+    o.acc = acc;
+    o.acc_cap = cap_cand;
+    o.sort_k[0] = sort_k[0];
+    o.sort_k[1] = sort_k[1];
+    o.sort_v[0] = sort_v[0];
+    o.sort_v[1] = sort_v[1];
+    o.trk_view = trk_view;
+    o.trk_moff = trk_moff;
+    o.view_trk = view_trk;
+    o.tracks = tracks;
+    o.out_members = out_members;
+    o.out_member_cap = (u64)std::max<long long>(N, 1);
+    return o;
+}
+
+et_status BatchRT::enqueue(cudaStream_t st, bool record) {
+    const Batch b = dev_batch();
+    const Work w = dev_work();
+    Out o = dev_out();
+    const long long n = N;
+    const size_t cells = (size_t)V * (size_t)ncell;
+    cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
+    if (n > 0) {
+        cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
+        launch_canonical_keys(b, keys[0], vals[0], st);
+        const int kb = b.vshift + bits_for((unsigned long long)std::max(V - 1, 0));
+        int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st);
+        u64 *sk = keys[c1], *ok = keys[c1 ^ 1];
+        u32 *sv = vals[c1], *ov = vals[c1 ^ 1];
+        launch_canonical_order(b, sk, sv, ok, ov, cell_count, st);
+        int c2 = radix_sort_pairs(ok, ov, sk, sv, n, bits_for((unsigned long long)(cells - 1)), temp, st);
+        launch_cell_order(b, c2 ? sv : ov, st);
+        exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st);
+        launch_seed_count(b, w, st);
+        exclusive_scan_u64(seed_off, seed_off, n, temp, &ctl->n_seeds, st);
+        launch_seed_fill(b, w, st);
+        launch_tube_count(b, w, record ? 1 : 0, st);
+        launch_cand_keys(b, w, st);
+        exclusive_scan_u64_dev(c_moff, c_moff, (long long)cap_cand, &ctl->n_cand, temp, &ctl->n_members, st);
+        launch_member_fill(b, w, st);
+        cudaMemsetAsync(best[0], 0xFF, sizeof(u64) * n, st);
+        cudaMemsetAsync(best[1], 0xFF, sizeof(u64) * n, st);
+        cudaMemsetAsync(owner, 0xFF, sizeof(int) * n, st);
+        cudaError_t e = launch_merge_coop(b, w, ctx->merge_grid, st);
+        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        launch_output(b, w, o, (long long)cap_cand, std::max<long long>(n, 1), temp, st);
+    } else {
+        cudaMemsetAsync(view_trk, 0, sizeof(long long) * (V + 1), st);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    return ET_OK;
+}
+
+et_status BatchRT::find(cudaStream_t st, bool use_graph) {
+    if (!loaded) return fail(ET_ERR_NOT_READY, "no grains loaded");
+    if (!st) st = ctx->stream;
+    et_status s;
+    if (use_graph && N > 0) {
+        const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V;
+        if (!gexec || key != graph_key) {
+            if (gexec) {
+                cudaGraphExecDestroy(gexec);
+                gexec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+            s = enqueue(st, false);
+            e = cudaStreamEndCapture(st, &g);
+            if (s != ET_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            e = cudaGraphInstantiate(&gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+            graph_key = key;
+        }
+        cudaError_t e = cudaGraphLaunch(gexec, st);
+        if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    } else {
+        s = enqueue(st, false);
+        if (s != ET_OK) return s;
+    }
+    cudaError_t e = cudaEventRecord(done, st);
+    if (e != cudaSuccess) return cuda_fail(e, "event record");
+    run_stream = st;
+    ran = true;
+    return ET_OK;
+}
+
+et_status BatchRT::read_ctl(Ctl &h) {
+    cudaError_t e = cudaEventSynchronize(done);
+    if (e != cudaSuccess) return cuda_fail(e, "wait for the view");
+    e = cudaMemcpy(&h, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read control block");
+    return ET_OK;
+}
+
+// Waits; on internal overflow grows the buffers and runs again (synchronously).
+et_status BatchRT::settle(bool record) {
+    if (!ran) return fail(ET_ERR_NOT_READY, "et_track_find was not called");
+    for (int attempt = 0;; ++attempt) {
+        et_status s = read_ctl(hctl);
+        if (s != ET_OK) return s;
+        if (hctl.error & ERRB_OUT_OF_RANGE) return fail(ET_ERR_OUT_OF_RANGE, "a grain lies outside [0, extent)");
+        if (hctl.error & ERRB_DUPLICATE) return fail(ET_ERR_DUPLICATE_GRAIN, "two grains share coordinates");
+        if (hctl.error & ERRB_TIMEOUT) return fail(ET_ERR_TIMEOUT, "device-side wait timed out in the merge");
+        if (!(hctl.error & ERRB_OVF_MASK)) return ET_OK;
+        if (attempt >= 6) return fail(ET_ERR_CAPACITY, "internal buffers kept overflowing");
+        if (hctl.error & ERRB_OVF_SEEDS) want_seeds = std::max<u64>(want_seeds, hctl.n_seeds + 1024);
+        if (hctl.error & ERRB_OVF_CAND) {
+            want_cand = std::max<u64>(want_cand, hctl.n_cand + 1024);
+            want_members = std::max<u64>(want_members, want_cand * 24);
+        }
+        if (hctl.error & ERRB_OVF_MEMBERS) want_members = std::max<u64>(want_members, hctl.n_members + 1024);
+        if (hctl.error & ERRB_OVF_RECORD) want_rec = std::max<u64>(want_rec, hctl.n_seeds);
+        s = reserve();
+        if (s != ET_OK) return s;
+        s = enqueue(ctx->stream, record);
+        if (s != ET_OK) return s;
+        cudaError_t e = cudaEventRecord(done, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "event record");
+        run_stream = ctx->stream;
+    }
+}
+
+et_status BatchRT::fetch(int64_t *view_off, et_track *out, int64_t cap, int64_t *n_tracks, int32_t *mem,
+                         int64_t mcap, int64_t *n_members) {
+    et_status s = settle(false);
+    if (s != ET_OK) return s;
+    const int64_t nt = (int64_t)hctl.n_acc, nm = (int64_t)hctl.n_out_members;
+    if (n_tracks) *n_tracks = nt;
+    if (n_members) *n_members = nm;
+    if ((nt > 0 && (!out || cap < nt)) || (nm > 0 && (!mem || mcap < nm)))
+        return fail(ET_ERR_CAPACITY, "need %lld tracks / %lld members", (long long)nt, (long long)nm);
+    cudaError_t e = cudaSuccess;
+    if (nt > 0) e = cudaMemcpy(out, tracks, sizeof(et_track) * nt, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && nm > 0) e = cudaMemcpy(mem, out_members, sizeof(int) * nm, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && view_off) {
+        std::vector<long long> tmp(V + 1);
+        e = cudaMemcpy(tmp.data(), view_trk, sizeof(long long) * (V + 1), cudaMemcpyDeviceToHost);
+        for (int v = 0; v <= V; ++v) view_off[v] = tmp[v];
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy results");
+    return ET_OK;
+}
+
+et_status BatchRT::seed_counts(int32_t *si, int32_t *sj, int32_t *cnt, int64_t cap, int64_t *n_seeds) {
+    et_status s = settle(false);
+    if (s != ET_OK) return s;
+    const u64 ns = hctl.n_seeds;
+    if (n_seeds) *n_seeds = (int64_t)ns;
+    if (ns > 0 && (!si || !sj || !cnt || (u64)cap < ns))
+        return fail(ET_ERR_CAPACITY, "need %llu seed records", (unsigned long long)ns);
+    want_rec = std::max<u64>(want_rec, ns + 1);
+    s = reserve();
+    if (s != ET_OK) return s;
+    s = enqueue(ctx->stream, true);
+    if (s != ET_OK) return s;
+    cudaEventRecord(done, ctx->stream);
+    run_stream = ctx->stream;
+    s = settle(true);
+    if (s != ET_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (ns > 0) {
+        e = cudaMemcpy(si, rec_lo, sizeof(int) * ns, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(sj, rec_hi, sizeof(int) * ns, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(cnt, rec_cnt, sizeof(int) * ns, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "copy seed records");
+    return ET_OK;
+}
+
+void BatchRT::stats(et_stats *o) const {
+    memset(o, 0, sizeof *o);
+    o->n_grains = N;
+    o->n_seeds = (int64_t)hctl.n_seeds;
+    o->n_tests = (int64_t)hctl.n_tests;
+    o->n_hits = (int64_t)hctl.n_hits;
+    o->n_candidates = (int64_t)hctl.n_cand;
+    o->n_members = (int64_t)hctl.n_members;
+    o->n_tracks = (int64_t)hctl.n_acc;
+    o->n_track_members = (int64_t)hctl.n_out_members;
+    o->merge_rounds = (int32_t)hctl.rounds;
+    for (int k = 0; k < 3; ++k) o->cell[k] = cs[k];
+}
+
+}  // namespace et
+
+// ==================================================================== C ABI
+
+using namespace et;
+
+struct et_ctx : public Ctx {};
+struct et_batch : public BatchRT {
+    using BatchRT::BatchRT;
+};
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                        \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        return fail(ET_ERR_OOM, "host allocation failed");               \
+    }                                                                    \
+    catch (...) {                                                        \
+        return fail(ET_ERR_CUDA, "unexpected exception in the runtime"); \
+    }
+
+extern "C" {
+
+int32_t et_abi_version(void) { return ET_ABI_VERSION; }
+
+const char *et_last_error(void) { return last_error(); }
+
+const char *et_status_string(et_status s) {
+    switch (s) {
+    case ET_OK: return "ok";
+    case ET_ERR_INVALID_ARG: return "invalid argument";
+    case ET_ERR_OUT_OF_RANGE: return "coordinate out of range";
+    case ET_ERR_DUPLICATE_GRAIN: return "duplicate grain";
+    case ET_ERR_PRECONDITION: return "parameters break the int32 cross-product bound";
+    case ET_ERR_CAPACITY: return "buffer too small";
+    case ET_ERR_OOM: return "out of device memory";
+    case ET_ERR_BUSY: return "busy";
+    case ET_ERR_TIMEOUT: return "device wait timed out";
+    case ET_ERR_CUDA: return "CUDA error";
+    case ET_ERR_NOT_READY: return "not ready";
+    default: return "unknown status";
+    }
+}
+
+et_status et_ctx_create(int device, et_ctx **out) {
+    GUARD_BEGIN
+    if (!out) return fail(ET_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        return fail(ET_ERR_CUDA, "no CUDA device available (%s)", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= n) return fail(ET_ERR_INVALID_ARG, "device %d of %d", device, n);
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    et_ctx *c = new et_ctx();
+    c->device = device;
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "stream create");
+    }
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+    cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+    c->merge_grid = merge_grid_blocks(device);
+    *out = c;
+    return ET_OK;
+    GUARD_END
+}
+
+et_status et_ctx_destroy(et_ctx *ctx) {
+    if (!ctx) return fail(ET_ERR_INVALID_ARG, "ctx is NULL");
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return ET_OK;
+}
+
+et_status et_ctx_set_allocator(et_ctx *ctx, et_alloc_fn alloc, et_free_fn free_fn, void *user) {
+    if (!ctx) return fail(ET_ERR_INVALID_ARG, "ctx is NULL");
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(ET_ERR_INVALID_ARG, "give both hooks or none");
+    ctx->alloc = alloc;
+    ctx->free_fn = free_fn;
+    ctx->user = user;
+    return ET_OK;
+}
+
+et_status et_ctx_info(et_ctx *ctx, int32_t *sm_count, int32_t *cc_major, int32_t *cc_minor) {
+    if (!ctx) return fail(ET_ERR_INVALID_ARG, "ctx is NULL");
+    if (sm_count) *sm_count = ctx->sms;
+    if (cc_major) *cc_major = ctx->cc_major;
+    if (cc_minor) *cc_minor = ctx->cc_minor;
+    return ET_OK;
+}
+
+et_status et_batch_create(et_ctx *ctx, const et_params *params, et_batch **out) {
+    GUARD_BEGIN
+    if (!ctx || !out) return fail(ET_ERR_INVALID_ARG, "ctx/out is NULL");
+    *out = nullptr;
+    et_status s = check_params(params);
+    if (s != ET_OK) return s;
+    cudaSetDevice(ctx->device);
+    *out = new et_batch(ctx, *params);
+    return ET_OK;
+    GUARD_END
+}
+
+et_status et_batch_destroy(et_batch *b) {
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    if (b->ran) cudaEventSynchronize(b->done);
+    delete b;
+    return ET_OK;
+}
+
+et_status et_batch_load(et_batch *b, const int32_t *xyz, const int64_t *offsets, int32_t n_views,
+                        int32_t on_device, void *stream) {
+    GUARD_BEGIN
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    cudaStream_t st = stream ? (cudaStream_t)stream : b->ctx->stream;
+    if (b->ran) cudaEventSynchronize(b->done);   // buffers may be reused
+    return b->load(xyz, offsets, n_views, on_device != 0, st);
+    GUARD_END
+}
+
+et_status et_batch_set_tuning(et_batch *b, const et_tuning *t) {
+    if (!b || !t) return fail(ET_ERR_INVALID_ARG, "batch/tuning is NULL");
+    for (int k = 0; k < 3; ++k)
+        if (t->cell[k] < 0) return fail(ET_ERR_INVALID_ARG, "cell[%d] < 0", k);
+    b->tune = *t;
+    b->loaded = false;   // the cell grid changes: reload required
+    return ET_OK;
+}
+
+et_status et_batch_find(et_batch *b, void *stream, int32_t use_graph) {
+    GUARD_BEGIN
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    return b->find((cudaStream_t)stream, use_graph != 0);
+    GUARD_END
+}
+
+et_status et_batch_fetch(et_batch *b, int64_t *view_track_offsets, et_track *tracks, int64_t cap,
+                         int64_t *n_tracks, int32_t *members, int64_t member_cap, int64_t *n_members) {
+    GUARD_BEGIN
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    return b->fetch(view_track_offsets, tracks, cap, n_tracks, members, member_cap, n_members);
+    GUARD_END
+}
+
+et_status et_batch_sync(et_batch *b) {
+    GUARD_BEGIN
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    return b->settle(false);
+    GUARD_END
+}
+
+et_status et_batch_stats(et_batch *b, et_stats *out) {
+    if (!b || !out) return fail(ET_ERR_INVALID_ARG, "batch/out is NULL");
+    b->stats(out);
+    return ET_OK;
+}
+
+// ---- views: batches of one
+
+et_status et_view_create(et_ctx *ctx, const int32_t *xyz, int64_t n, const et_params *params, et_view **out) {
+    if (n < 0) return fail(ET_ERR_INVALID_ARG, "n < 0");
+    et_status s = et_batch_create(ctx, params, out);
+    if (s != ET_OK) return s;
+    int64_t off[2] = {0, n};
+    s = et_batch_load(*out, xyz, off, 1, 0, nullptr);
+    if (s == ET_OK) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);   // the caller may free xyz on return
+        if (e != cudaSuccess) s = cuda_fail(e, "grain upload");
+    }
+    if (s != ET_OK) {
+        et_batch_destroy(*out);
+        *out = nullptr;
+    }
+    return s;
+}
+
+et_status et_view_create_device(et_ctx *ctx, const int32_t *d_xyz, int64_t n, const et_params *params,
+                                et_view **out) {
+    if (n < 0) return fail(ET_ERR_INVALID_ARG, "n < 0");
+    et_status s = et_batch_create(ctx, params, out);
+    if (s != ET_OK) return s;
+    int64_t off[2] = {0, n};
+    s = et_batch_load(*out, d_xyz, off, 1, 1, nullptr);
+    if (s != ET_OK) {
+        et_batch_destroy(*out);
+        *out = nullptr;
+    }
+    return s;
+}
+
+et_status et_view_load(et_view *view, const int32_t *xyz, int64_t n, void *stream) {
+    if (n < 0) return fail(ET_ERR_INVALID_ARG, "n < 0");
+    int64_t off[2] = {0, n};
+    return et_batch_load(view, xyz, off, 1, 0, stream);
+}
+
+et_status et_view_destroy(et_view *view) { return et_batch_destroy(view); }
+
+et_status et_track_find(et_view *view, void *stream) { return et_batch_find(view, stream, 0); }
+
+et_status et_track_fetch(et_view *view, et_track *tracks, int64_t cap, int64_t *n_tracks, int32_t *members,
+                         int64_t member_cap, int64_t *n_members) {
+    return et_batch_fetch(view, nullptr, tracks, cap, n_tracks, members, member_cap, n_members);
+}
+
+et_status et_view_seed_counts(et_view *view, int32_t *seed_i, int32_t *seed_j, int32_t *count, int64_t cap,
+                              int64_t *n_seeds) {
+    GUARD_BEGIN
+    if (!view) return fail(ET_ERR_INVALID_ARG, "view is NULL");
+    cudaSetDevice(view->ctx->device);
+    return view->seed_counts(seed_i, seed_j, count, cap, n_seeds);
+    GUARD_END
+}
+
+}  // extern "C"

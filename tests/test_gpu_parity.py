@@ -1,0 +1,292 @@
+"""GPU path vs the oracle, through the C ABI (libet.so).
+
+Counts, candidate sets and track lists must be bit-identical; the FP32 fit is
+compared with the FP64 oracle fit within the stated tolerance:
+    |u32 - u64|_inf <= 1e-5,
+    |c32 - c64|_inf <= 1e-5 * max(1, |c64|_inf),
+    |t32 - t64|     <= 1e-5 * max(1, t64max - t64min),
+for tracks whose scatter matrix is well conditioned (lambda1 >= 100 lambda2).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1311_5334_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+@pytest.fixture(scope="module")
+def et():
+    from paper_1311_5334_gb300 import et as E
+    E.lib()
+    return E
+
+
+@pytest.fixture(scope="module")
+def ctx(et):
+    c = et.Context(0)
+    yield c
+    c.close()
+
+
+def run_view(et, ctx, xyz, params, cell=None, seeds=False):
+    v = et.View.create(ctx, xyz, params)
+    try:
+        if cell is not None:
+            v.set_tuning(cell)
+            v.load_host(xyz)
+        v.find()
+        tracks, members = v.fetch()
+        st = v.stats()
+        sc = v.seed_counts() if seeds else None
+    finally:
+        v.close()
+    return tracks, members, st, sc
+
+
+def oracle_run(O, xyz, params, keep_seeds=False):
+    o = O.Oracle(xyz, params["extent"], params["seed_min"], params["seed_max"], params["tube_r"],
+                 params["min_hits"])
+    try:
+        return o.find_tracks(keep_seeds=keep_seeds)
+    finally:
+        o.close()
+
+
+def seed_table(lo, hi, cnt):
+    order = np.lexsort((hi, lo))
+    return np.stack([lo[order], hi[order], cnt[order]], axis=1)
+
+
+def check_fit(tracks, want, tol=1e-5):
+    assert len(tracks) == len(want)
+    for k in range(len(want)):
+        lam = want.lam[k]
+        if lam[0] < 100 * max(lam[1], 1e-300):
+            continue
+        u32, u64 = tracks["u"][k].astype(np.float64), want.u[k]
+        assert np.max(np.abs(u32 - u64)) <= tol, (k, u32, u64)
+        c32, c64 = tracks["c"][k].astype(np.float64), want.c[k]
+        assert np.max(np.abs(c32 - c64)) <= tol * max(1.0, np.max(np.abs(c64))), (k, c32, c64)
+        L = max(1.0, want.t[k][1] - want.t[k][0])
+        assert abs(tracks["tmin"][k] - want.t[k][0]) <= tol * L
+        assert abs(tracks["tmax"][k] - want.t[k][1]) <= tol * L
+
+
+def assert_same(et, tracks, members, want):
+    got = et.track_tuples(tracks, members)
+    exp = want.as_tuples()
+    assert len(got) == len(exp)
+    assert got == exp
+
+
+# ------------------------------------------------------------------ worked examples
+
+def _cases():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _cases(), ids=lambda c: c["name"])
+def test_worked_examples(et, ctx, case):
+    p = dict(extent=case["extent"], seed_min=case["seed_min"], seed_max=case["seed_max"],
+             tube_r=case["tube_r"], min_hits=case["min_hits"])
+    tracks, members, st, (si, sj, sc) = run_view(et, ctx, np.asarray(case["grains"]), p, seeds=True)
+    want_seeds = sorted(tuple(s) for s in case["seeds"])
+    assert sorted(zip(si.tolist(), sj.tolist(), sc.tolist())) == want_seeds
+    got = et.track_tuples(tracks, members)
+    assert got == [(a, b, n, tuple(m)) for a, b, n, m in case["tracks"]]
+
+
+# ------------------------------------------------------------------ small random vs brute force
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_views_vs_brute_force(et, ctx, seed):
+    from oracle import brute
+    from tests.test_oracle_pins import _small_view
+    rng = np.random.default_rng(100 + seed)
+    extent = (1500, 1200, 400)
+    xyz = _small_view(rng, extent, n_fog=60 + 20 * seed, tracks=3 + seed % 3, gap=37)
+    smin, smax, r, h = [(40, 200, 6, 4), (0, 150, 10, 5), (60, 400, 3, 3), (40, 200, 0, 2),
+                        (30, 250, 8, 6), (10, 120, 15, 4)][seed]
+    bs, bt = brute.find(xyz, smin, smax, r, h)
+    p = dict(extent=extent, seed_min=smin, seed_max=smax, tube_r=r, min_hits=h)
+    for cell in [None, (97, 131, 53), (400, 400, 400), (17, 1200, 9), (1, 1, 1)]:
+        tracks, members, st, (si, sj, sc) = run_view(et, ctx, xyz, p, cell=cell, seeds=True)
+        assert {(int(a), int(b)): int(c) for a, b, c in zip(si, sj, sc)} == bs
+        assert et.track_tuples(tracks, members) == bt
+
+
+# ------------------------------------------------------------------ paper-shaped workloads
+
+@pytest.mark.parametrize("workload", ["pr1", "dense"])
+def test_workload_parity(et, ctx, oracle_mod, workload):
+    v = synth.pr1() if workload == "pr1" else synth.dense()
+    p = synth.params(v.extent)
+    want, (olo, ohi, ocnt) = oracle_run(oracle_mod, v.xyz, p, keep_seeds=True)
+    tracks, members, st, (si, sj, sc) = run_view(et, ctx, v.xyz, p, seeds=True)
+    assert st["n_seeds"] == want.n_seeds
+    assert np.array_equal(seed_table(si, sj, sc), seed_table(olo, ohi, ocnt))
+    assert st["n_hits"] == int(ocnt.sum())
+    assert st["n_candidates"] == want.n_cand
+    assert_same(et, tracks, members, want)
+    check_fit(tracks, want)
+
+
+@pytest.mark.parametrize("cell", [(150, 150, 150), (300, 300, 100), (600, 600, 600), (1000, 250, 125),
+                                  (2000, 2000, 2000)])
+def test_cell_size_invariance(et, ctx, oracle_mod, cell):
+    v = synth.dense()
+    p = synth.params(v.extent)
+    want = oracle_run(oracle_mod, v.xyz, p)
+    tracks, members, st, _ = run_view(et, ctx, v.xyz, p, cell=cell)
+    assert tuple(st["cell"]) == cell
+    assert st["n_seeds"] == want.n_seeds
+    assert_same(et, tracks, members, want)
+
+
+def test_permutation_invariance(et, ctx):
+    v = synth.pr1()
+    p = synth.params(v.extent)
+    rng = np.random.default_rng(4)
+    perm = rng.permutation(v.n)
+    t1, m1, _, _ = run_view(et, ctx, v.xyz, p)
+    t2, m2, _, _ = run_view(et, ctx, v.xyz[perm], p)
+    a = et.track_tuples(t1, m1)
+    b = [(int(perm[i]), int(perm[j]), n, tuple(sorted(int(perm[x]) for x in mem)))
+         for i, j, n, mem in et.track_tuples(t2, m2)]
+    assert a == b
+    assert np.array_equal(t1["u"], t2["u"]) and np.array_equal(t1["tmin"], t2["tmin"])
+
+
+# ------------------------------------------------------------------ batched form
+
+def test_batched_matches_oracle_per_view(et, ctx, oracle_mod):
+    views = synth.batched(n_views=24, seed=3)
+    views = [v for v in views if v.n < 20000][:16]
+    xyz, offs = synth.concat(views)
+    p = synth.params(views[0].extent)
+    b = et.Batch(ctx, p)
+    try:
+        b.load(xyz, offs)
+        for use_graph in (False, True, True):
+            b.find(use_graph=use_graph)
+            tracks, members, voff = b.fetch()
+            for k, v in enumerate(views):
+                want = oracle_run(oracle_mod, v.xyz, p)
+                sub = tracks[voff[k]:voff[k + 1]]
+                assert np.all(sub["view"] == k)
+                assert et.track_tuples(sub, members) == want.as_tuples()
+    finally:
+        b.close()
+
+
+# ------------------------------------------------------------------ edge cases
+
+def _p(extent=(1000, 1000, 1000), smin=10, smax=300, r=5, h=3):
+    return dict(extent=extent, seed_min=smin, seed_max=smax, tube_r=r, min_hits=h)
+
+
+def test_empty_and_tiny_views(et, ctx):
+    for xyz in [np.zeros((0, 3)), np.array([[5, 5, 5]]), np.array([[5, 5, 5], [900, 900, 900]])]:
+        tracks, members, st, _ = run_view(et, ctx, xyz, _p())
+        assert len(tracks) == 0 and len(members) == 0 and st["n_seeds"] == 0
+    tracks, members, st, (si, sj, sc) = run_view(et, ctx, np.array([[50, 5, 5], [5, 5, 5]]), _p(h=2), seeds=True)
+    assert st["n_seeds"] == 1 and list(zip(si, sj, sc)) == [(1, 0, 2)]
+    assert et.track_tuples(tracks, members) == [(1, 0, 2, (0, 1))]
+
+
+def test_long_collinear_line(et, ctx, oracle_mod):
+    """4000 collinear grains: every seed holds all of them; one track."""
+    n = 4000
+    xyz = np.stack([np.arange(n) * 3 + 7, np.arange(n) * 2 + 11, np.full(n, 40)], axis=1)
+    p = _p(extent=(20000, 20000, 100), smin=10, smax=60, r=0, h=5)
+    tracks, members, st, _ = run_view(et, ctx, xyz, p)
+    want = oracle_run(oracle_mod, xyz, p)
+    assert len(want) == 1 and want.nhits[0] == n
+    assert_same(et, tracks, members, want)
+
+
+def test_clustered_view_forces_buffer_growth(et, ctx, oracle_mod):
+    """All grains in 1 % of the volume: the uniform-density estimates of the
+    seed/candidate buffers are far too small and the runtime must grow them."""
+    rng = np.random.default_rng(21)
+    pts = set()
+    while len(pts) < 3000:
+        pts.add(tuple(int(x) for x in rng.integers(0, 600, 3)))
+    base = np.array(sorted(pts)) + np.array([1000, 1000, 200])
+    line = np.stack([np.arange(80) * 7 + 1000, np.arange(80) * 5 + 1000, np.full(80, 500)], axis=1)
+    xyz = np.unique(np.concatenate([base, line]), axis=0)
+    xyz = xyz[rng.permutation(len(xyz))]
+    p = _p(extent=(30000, 30000, 5000), smin=20, smax=200, r=6, h=6)
+    want = oracle_run(oracle_mod, xyz, p)
+    tracks, members, st, _ = run_view(et, ctx, xyz, p)
+    assert st["n_seeds"] == want.n_seeds
+    assert_same(et, tracks, members, want)
+
+
+def test_input_errors(et, ctx):
+    with pytest.raises(et.EtError) as e:
+        v = et.View.create(ctx, np.array([[1, 2, 3], [1000, 2, 3]]), _p())
+        try:
+            v.find()
+            v.fetch()
+        finally:
+            v.close()
+    assert e.value.status == et.OUT_OF_RANGE
+    with pytest.raises(et.EtError) as e:
+        v = et.View.create(ctx, np.array([[1, 2, 3], [4, 5, 6], [1, 2, 3]]), _p())
+        try:
+            v.find()
+            v.fetch()
+        finally:
+            v.close()
+    assert e.value.status == et.DUPLICATE_GRAIN
+    with pytest.raises(et.EtError) as e:
+        et.View.create(ctx, np.zeros((1, 3)), _p(extent=(2 ** 21, 2 ** 21, 10), smax=600))
+    assert e.value.status == et.PRECONDITION
+    with pytest.raises(et.EtError) as e:
+        et.View.create(ctx, np.zeros((1, 3)), _p(h=0))
+    assert e.value.status == et.INVALID_ARG
+
+
+def test_torch_allocator_same_result(et, oracle_mod):
+    import torch
+    v = synth.pr1()
+    p = synth.params(v.extent)
+    want = oracle_run(oracle_mod, v.xyz, p)
+    before = torch.cuda.memory_allocated(0)
+    with et.Context(0, use_torch_allocator=True) as c2:
+        view = c2.view(v.xyz, p)
+        assert torch.cuda.memory_allocated(0) > before
+        view.find()
+        tracks, members = view.fetch()
+        view.close()
+    assert_same(et, tracks, members, want)
+
+
+# ------------------------------------------------------------------ served form
+
+def test_server_results_match_oracle(et, ctx, oracle_mod):
+    views = [v for v in synth.batched(n_views=40, seed=4) if v.n < 15000][:20]
+    p = synth.params(views[0].extent)
+    with ctx.server(p, mem_budget_bytes=2 << 30, max_batch_views=8) as s:
+        for k, v in enumerate(views):
+            assert s.submit(v.xyz, tag=1000 + k) == et.OK
+        got = {}
+        for _ in range(2000):
+            for r in s.poll(max_results=64, timeout_us=100000):
+                assert r.status == et.OK
+                assert r.t_submit_ns <= r.t_admit_ns <= r.t_done_ns
+                got[r.tag] = s.fetch(r.tag)
+            if len(got) == len(views):
+                break
+    assert len(got) == len(views)
+    for k, v in enumerate(views):
+        tracks, members = got[1000 + k]
+        assert et.track_tuples(tracks, members) == oracle_run(oracle_mod, v.xyz, p).as_tuples()
