@@ -11,10 +11,15 @@
 // rejected.  The others post their key on each unused grain (atomicMin).  A
 // candidate holding the minimum key on all its unused grains is "ready": every
 // earlier candidate sharing one of those grains is already decided, so its
-// unused set is final and it is accepted (it passed the count).  Ready
-// candidates share no unused grain, so they mark their grains in parallel.
-// The lowest undecided key is always ready, so every round decides at least
-// one candidate.
+// unused set is final.  It recounts that set -- a candidate accepted earlier
+// in the same phase may have taken some of its grains -- and is accepted iff
+// at least min_hits remain, else rejected.  Ready candidates share no unused
+// grain, so they mark their grains in parallel.  The lowest undecided key is
+// always ready, so every round decides at least one candidate.
+//
+// Key slots are cleaned by their posters: a candidate decided in phase 2
+// resets the slots it holds; one still undecided resets last round's slots of
+// all its grains at the start of the next round.
 //
 // Rounds are separated by a grid barrier in one cooperative launch; every
 // wait is bounded and a timeout sets ERRB_TIMEOUT instead of hanging.
@@ -104,7 +109,6 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
                     if (__ldcg(&w.owner[g]) < 0) atomicMin(&B[g], key);
                 }
             }
-            if (lane == 0) w.c_nfree[c] = nfree;
             ++my_active;
         }
         if (lane == 0 && my_active) atomicAdd(&ctl->active[round & 1], my_active);
@@ -121,30 +125,39 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             const u64 key = w.c_key[c];
             bool ready = true;
+            u32 nfree = 0;
             for (u64 base = m0; base < m1; base += 32) {
                 const u64 m = base + lane;
-                bool bad = false;
+                bool fr = false, bad = false;
                 if (m < m1) {
                     const int g = w.members[m];
-                    bad = __ldcg(&w.owner[g]) < 0 && __ldcg(&B[g]) != key;
+                    fr = __ldcg(&w.owner[g]) < 0;
+                    bad = fr && __ldcg(&B[g]) != key;
                 }
                 if (__any_sync(0xffffffffu, bad)) {
                     ready = false;
                     break;
                 }
+                nfree += __popc(__ballot_sync(0xffffffffu, fr));
             }
             if (!ready) continue;
+            // ready: the unused grains are exactly those where this key is the
+            // minimum; nobody else can take them any more
+            const bool accept = nfree >= H;
             for (u64 base = m0; base < m1; base += 32) {
                 const u64 m = base + lane;
                 if (m < m1) {
                     const int g = w.members[m];
                     if (__ldcg(&w.owner[g]) < 0) {
-                        w.owner[g] = (int)c;
+                        if (accept) w.owner[g] = (int)c;
                         B[g] = ~0ull;
                     }
                 }
             }
-            if (lane == 0) w.c_state[c] = CS_ACCEPTED;
+            if (lane == 0) {
+                w.c_nfree[c] = nfree;
+                w.c_state[c] = accept ? CS_ACCEPTED : CS_REJECTED;
+            }
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
     }

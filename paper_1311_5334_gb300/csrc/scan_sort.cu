@@ -31,7 +31,7 @@ __device__ __forceinline__ T warp_incl_scan(T v) {
 // and the block total.
 template <class T>
 __device__ __forceinline__ T block_excl_scan(T v, T &total) {
-    __shared__ T warp_sum[32];
+    __shared__ T warp_sum[33];   // 32 warp prefixes + the block total
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T inc = warp_incl_scan(v);
     if (lane == 31) warp_sum[wid] = inc;
@@ -40,11 +40,11 @@ __device__ __forceinline__ T block_excl_scan(T v, T &total) {
         T s = lane < nw ? warp_sum[lane] : T(0);
         T si = warp_incl_scan(s);
         if (lane < nw) warp_sum[lane] = si - s;
-        if (lane == nw - 1) warp_sum[31] = si;
+        if (lane == nw - 1) warp_sum[32] = si;
     }
     __syncthreads();
     T res = warp_sum[wid] + inc - v;
-    total = warp_sum[31];
+    total = warp_sum[32];
     __syncthreads();
     return res;
 }
