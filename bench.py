@@ -1,0 +1,382 @@
+"""Benchmark of the track-finding hot path on GB300 (one JSON line on stdout).
+
+Step = one pass of the whole path (canonical order + cell list, seeds, tube
+counts, candidates + member lists, merge, fit/output) over one batch of 256
+synthetic views of 300x300x50 um (lognormal grain counts, median 10k, range
+2k-50k, isotropic tracks at 1 % of the grains, seed 3), run as one batched
+launch sequence replayed from a CUDA graph, with the grains already resident
+in device memory.  L2 is flushed (256 MiB write) between timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain restatement of the method)
+on the machine's host cores, on a bounded sample of the same workload per step.
+For N > 1 (torchrun) each rank processes its own batch (weak scaling, no
+data-path collective); the timed region is bracketed by barriers and the
+maximum over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1311_5334_gb300 import synth  # noqa: E402
+
+VIEW_CM2 = 300e-4 * 300e-4          # one 300 x 300 um view in cm^2
+WORKLOAD = ("batched: 256 views 300x300x50 um, fog lognormal (median 10k, sigma 0.6, 2k-50k), "
+            "isotropic through-going tracks at 1% of the fog count, gaps 3.3 um, jitter 0.05/0.3 um, "
+            "int32 10 nm coords, seed window 5-20 um, tube 0.4 um, min hits 8, seed 3")
+METRIC = "views/s"
+# One tube-membership test: 3 IADD (offset), 6 IMUL/IMAD (int32 cross product),
+# 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
+OPS_PER_TEST = 14
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+WORKLOADS = {
+    "batched": WORKLOAD,
+    "dense": ("dense: one view 300x300x50 um, 20,000 fog + 200 isotropic through-going tracks (gaps 3.3 um) "
+              "+ 100 short tracks (range 10-50 um, gaps 1.6 um), jitter 0.05/0.3 um, int32 10 nm coords, "
+              "seed window 5-20 um, tube 0.4 um, min hits 8, seed 2"),
+    "pr1": ("PR1: one view 300x300x50 um, 2,000 fog + 20 isotropic tracks (gaps 3.3 um), jitter 0.05/0.3 um, "
+            "int32 10 nm coords, seed window 5-20 um, tube 0.4 um, min hits 8, seed 1"),
+}
+
+
+def make_workload(name="batched"):
+    if name == "dense":
+        views = [synth.dense()]
+    elif name == "pr1":
+        views = [synth.pr1()]
+    else:
+        views = synth.batched(n_views=256, seed=3)
+    xyz, offs = synth.concat(views)
+    return views, xyz, offs
+
+
+def oracle_views_per_s(views, budget_s, start=0):
+    """Times the oracle on views[start:] until budget_s of wall time is used."""
+    from oracle import oracle as O
+    O.build()
+    p = synth.params(views[0].extent)
+    done, seeds, t_used = 0, 0, 0.0
+    k = start
+    names = []
+    while t_used < budget_s and done < len(views):
+        v = views[k % len(views)]
+        t0 = time.perf_counter()
+        with O.Oracle(v.xyz, v.extent, p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"]) as o:
+            tr = o.find_tracks()
+        t_used += time.perf_counter() - t0
+        done += 1
+        seeds += tr.n_seeds
+        names.append(k % len(views))
+        k += 1
+    return done, seeds, t_used, names
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    views, _, _ = make_workload(args.workload)
+    cores = os.cpu_count()
+    per_step = max(1.0, float(os.environ.get("ET_REF_STEP_S", "4")))
+    k = 0
+    for _ in range(args.warmup):
+        d, _, _, _ = oracle_views_per_s(views, per_step / 4, start=k)
+        k += d
+    tot_v, tot_s, tot_t = 0, 0, 0.0
+    for _ in range(args.steps):
+        d, s, t, _ = oracle_views_per_s(views, per_step, start=k)
+        k += d
+        tot_v += d
+        tot_s += s
+        tot_t += t
+    value = tot_v / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": {"workload": WORKLOADS[args.workload],
+                                            "parallelism": "oracle on host cores"},
+            "seeds_per_s": tot_s / tot_t,
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{tot_v} views of the {len(views)}-view step, consecutive from view 0, "
+                                       f"~{per_step:.0f} s per step"},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_1311_5334_gb300 import et
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    views, xyz_h, offs = make_workload(args.workload)
+    n_views = len(views)
+    params = synth.params(views[0].extent)
+    # a dedicated stream: the legacy default stream (handle 0) would mean
+    # "the context's own stream" to the library
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = et.Context(local)
+    info = ctx.info()
+    xyz_d = torch.from_numpy(xyz_h).cuda()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    batch = et.Batch(ctx, params)
+    batch.set_profiling(True)
+    if args.cell:
+        batch.set_tuning(tuple(int(c) for c in args.cell.split(",")))
+    batch.load(xyz_d, offs, stream=stream)
+
+    def step():
+        batch.load(xyz_d, offs, stream=stream)
+        batch.find(stream=stream, use_graph=True)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+        batch.sync()
+        flush.zero_()
+    ref_stats = batch.stats()
+
+    # timed region: per-step CUDA events on the launching stream, L2 flushed between steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall0 = time.perf_counter()
+    step_ms, tube_ms = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        batch.sync()                       # status check (device idle afterwards)
+        st = batch.stats()
+        step_ms.append(e0.elapsed_time(e1))
+        tube_ms.append(st["stage_ms"]["tube_count"])
+        assert st["n_seeds"] == ref_stats["n_seeds"] and st["n_tracks"] == ref_stats["n_tracks"]
+        flush.zero_()
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = float(np.sum(step_ms))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n_views / (ms_per_step / 1e3)
+    seeds_per_s = ws * ref_stats["n_seeds"] / (ms_per_step / 1e3)
+
+    # roofline of the dominant kernel (tube counts): integer ALU issue
+    tube_avg_ms = float(np.mean(tube_ms))
+    ops = OPS_PER_TEST * ref_stats["n_tests"]
+    achieved = ops / (tube_avg_ms / 1e3) / 1e12
+    peak = info["sm_count"] * 128 * 2070e6 / 1e12
+    stage_ms = ref_stats["stage_ms"]
+
+    line_extra = {}
+    if args.no_extra:
+        plain_views_per_s = e2e_val = None
+        h2d = d2h = 0
+    else:
+        plain_views_per_s, e2e_val, h2d, d2h = extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws)
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "views_per_step": n_views,
+                       "grains_per_step": int(offs[-1]),
+                       "seeds_per_step": ref_stats["n_seeds"], "tube_tests_per_step": ref_stats["n_tests"],
+                       "tracks_per_step": ref_stats["n_tracks"], "cell_units": list(ref_stats["cell"]),
+                       "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
+                       "parallelism": f"replicas: one {n_views}-view batch per rank x {ws}"},
+            "seeds_per_s": seeds_per_s,
+            "cm2_per_h": value * VIEW_CM2 * 3600,
+            "plain_views_per_s": plain_views_per_s,
+            "stage_ms": stage_ms,
+            "wall_s": wall,
+            "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
+                         "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                         "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
+                                  f"{tube_avg_ms:.3f} ms (in-graph CUDA events); peak = "
+                                  f"{info['sm_count']} SMs x 128 lanes x 2070 MHz"},
+            "e2e": {"value": e2e_val, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(ref_stats["kernel_launches"]) * args.steps,
+            "clocks": clk}
+    line.update(line_extra)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra:
+        budget = float(os.environ.get("ET_CPU_BASELINE_S", "15"))
+        d, s, t, names = oracle_views_per_s(views, budget)
+        line["cpu_baseline"] = {"value": d / t, "unit": "views/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"views {names[0]}..{names[-1]} ({d} of {n_views}) of the step, "
+                                          f"{t:.1f} s; counting parallel over all cores (OpenMP), "
+                                          "merge and fit single-threaded"}
+    batch.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws):
+    """Plain one-view-per-launch form and the end-to-end (host buffers) form."""
+    import torch
+    from paper_1311_5334_gb300 import et
+    n_views = len(views)
+    # plain form: one view per launch sequence, same views, device-resident
+    plain = et.Batch(ctx, params)
+    plain_ms = 0.0
+    n_plain = min(n_views, int(os.environ.get("ET_PLAIN_VIEWS", "256")))
+    for k in range(n_plain):
+        o0, o1 = int(offs[k]), int(offs[k + 1])
+        sub = xyz_d[o0:o1]
+        plain.load(sub, [0, o1 - o0], stream=stream)   # warm buffers for this size
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plain.load(sub, [0, o1 - o0], stream=stream)
+        plain.find(stream=stream)
+        e1.record(stream)
+        plain.sync()
+        plain_ms += e0.elapsed_time(e1)
+    plain.close()
+    plain_views_per_s = n_plain / (plain_ms / 1e3)
+
+    # e2e: host (pinned) grains in, tracks + members out, through the C ABI
+    pinned = torch.from_numpy(xyz_h).pin_memory()
+    host_view = pinned.numpy()
+    eb = et.Batch(ctx, params)
+    eb.load(host_view, offs)
+    eb.find(use_graph=True)
+    tr, mem, voff = eb.fetch()
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        eb.load(host_view, offs)
+        eb.find(use_graph=True)
+        tr, mem, voff = eb.fetch()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    eb.close()
+    h2d = xyz_h.nbytes + offs.nbytes
+    d2h = tr.nbytes + mem.nbytes + voff.nbytes + 2 * 256
+    e2e_val = ws * n_views / e2e_s
+    return plain_views_per_s, e2e_val, h2d, d2h
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="time only the device-resident step (no plain/e2e/cpu baseline); for profilers")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched")
+    ap.add_argument("--cell", default="", help="cell edges x,y,z in coordinate units (default: automatic)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

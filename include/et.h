@@ -115,6 +115,12 @@ typedef struct {
     int64_t n_track_members;
     int32_t merge_rounds;
     int32_t cell[3];        /* cell edge actually used */
+    int32_t kernel_launches;/* kernels one run of the path launches (from its captured graph) */
+    int32_t profiled;       /* 1 if stage_ms holds timings of the last run */
+    /* with profiling on: CUDA-event time of each stage of the last run, ms:
+     * 0 canonical order + cell list, 1 seeds, 2 tube counts, 3 candidate keys
+     * + member lists, 4 merge, 5 output (order, fit, members) */
+    float stage_ms[6];
 } et_stats;
 
 typedef struct et_ctx et_ctx;
@@ -202,6 +208,9 @@ et_status et_batch_fetch(et_batch *b, int64_t *view_track_offsets, et_track *tra
                          int64_t *n_tracks, int32_t *members, int64_t member_cap,
                          int64_t *n_members);
 et_status et_batch_stats(et_batch *b, et_stats *out);
+/* on != 0: record a CUDA event between the stages of every later run (also
+ * inside captured graphs) so that et_batch_stats reports stage times. */
+et_status et_batch_set_profiling(et_batch *b, int32_t on);
 /* Waits for the batch without copying anything back; returns the run status. */
 et_status et_batch_sync(et_batch *b);
 et_status et_batch_destroy(et_batch *b);

@@ -125,6 +125,8 @@ BatchRT::BatchRT(Ctx *c, const et_params &pp) : ctx(c), p(pp) {
 BatchRT::~BatchRT() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (done) cudaEventDestroy(done);
+    for (cudaEvent_t &e : ev)
+        if (e) cudaEventDestroy(e);
     for (Group *g : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
         g->release(ctx);
 }
@@ -408,6 +410,7 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
     Out o = dev_out();
     const long long n = N;
     const size_t cells = (size_t)V * (size_t)ncell;
+    mark(0, st);
     cudaMemsetAsync(ctl, 0, sizeof(Ctl), st);
     if (n > 0) {
         cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
@@ -420,19 +423,25 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         int c2 = radix_sort_pairs(ok, ov, sk, sv, n, bits_for((unsigned long long)(cells - 1)), temp, st);
         launch_cell_order(b, c2 ? sv : ov, st);
         exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st);
+        mark(1, st);
         launch_seed_count(b, w, st);
         exclusive_scan_u64(seed_off, seed_off, n, temp, &ctl->n_seeds, st);
         launch_seed_fill(b, w, st);
+        mark(2, st);
         launch_tube_count(b, w, record ? 1 : 0, st);
+        mark(3, st);
         launch_cand_keys(b, w, st);
         exclusive_scan_u64_dev(c_moff, c_moff, (long long)cap_cand, &ctl->n_cand, temp, &ctl->n_members, st);
         launch_member_fill(b, w, st);
         cudaMemsetAsync(best[0], 0xFF, sizeof(u64) * n, st);
         cudaMemsetAsync(best[1], 0xFF, sizeof(u64) * n, st);
         cudaMemsetAsync(owner, 0xFF, sizeof(int) * n, st);
+        mark(4, st);
         cudaError_t e = launch_merge_coop(b, w, ctx->merge_grid, st);
         if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        mark(5, st);
         launch_output(b, w, o, (long long)cap_cand, std::max<long long>(n, 1), temp, st);
+        mark(6, st);
     } else {
         cudaMemsetAsync(view_trk, 0, sizeof(long long) * (V + 1), st);
     }
@@ -446,7 +455,8 @@ et_status BatchRT::find(cudaStream_t st, bool use_graph) {
     if (!st) st = ctx->stream;
     et_status s;
     if (use_graph && N > 0) {
-        const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V;
+        const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V ^
+                                       (profile ? 0x8000000000000000ull : 0ull);
         if (!gexec || key != graph_key) {
             if (gexec) {
                 cudaGraphExecDestroy(gexec);
@@ -477,6 +487,7 @@ et_status BatchRT::find(cudaStream_t st, bool use_graph) {
     if (e != cudaSuccess) return cuda_fail(e, "event record");
     run_stream = st;
     ran = true;
+    profiled_run = profile;
     return ET_OK;
 }
 
@@ -563,7 +574,54 @@ et_status BatchRT::seed_counts(int32_t *si, int32_t *sj, int32_t *cnt, int64_t c
     return ET_OK;
 }
 
-void BatchRT::stats(et_stats *o) const {
+void BatchRT::mark(int stage, cudaStream_t st) {
+    if (!profile) return;
+    if (!ev[stage]) cudaEventCreate(&ev[stage]);
+    // inside stream capture a plain record only expresses a dependency; an
+    // external record becomes an event node that fires on every replay
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[stage], st, cudaEventRecordExternal);
+    else cudaEventRecord(ev[stage], st);
+}
+
+// Number of kernels in one run of the path: capture the launch sequence into
+// a graph that is never executed and count its kernel nodes.
+int BatchRT::count_kernels() {
+    const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V;
+    if (kernel_launches >= 0 && key == launches_key) return kernel_launches;
+    if (!loaded || N == 0) return 0;
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -1;
+    const bool prof = profile;
+    profile = false;
+    cudaGraph_t g = nullptr;
+    int count = -1;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        et_status s = enqueue(st, false);
+        cudaStreamEndCapture(st, &g);
+        if (s == ET_OK && g) {
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(g, nodes.data(), &nn);
+            count = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++count;
+            }
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    profile = prof;
+    cudaStreamDestroy(st);
+    kernel_launches = count;
+    launches_key = key;
+    return count;
+}
+
+void BatchRT::stats(et_stats *o) {
     memset(o, 0, sizeof *o);
     o->n_grains = N;
     o->n_seeds = (int64_t)hctl.n_seeds;
@@ -575,6 +633,19 @@ void BatchRT::stats(et_stats *o) const {
     o->n_track_members = (int64_t)hctl.n_out_members;
     o->merge_rounds = (int32_t)hctl.rounds;
     for (int k = 0; k < 3; ++k) o->cell[k] = cs[k];
+    o->kernel_launches = count_kernels();
+    o->profiled = 0;
+    if (profiled_run && ran) {
+        cudaEventSynchronize(done);
+        bool ok = true;
+        for (int k = 0; k < NSTAGE; ++k) {
+            float ms = 0;
+            if (!ev[k] || !ev[k + 1] || cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) != cudaSuccess) ok = false;
+            o->stage_ms[k] = ms;
+        }
+        cudaGetLastError();
+        o->profiled = ok ? 1 : 0;
+    }
 }
 
 }  // namespace et
@@ -742,8 +813,17 @@ et_status et_batch_sync(et_batch *b) {
 }
 
 et_status et_batch_stats(et_batch *b, et_stats *out) {
+    GUARD_BEGIN
     if (!b || !out) return fail(ET_ERR_INVALID_ARG, "batch/out is NULL");
+    cudaSetDevice(b->ctx->device);
     b->stats(out);
+    return ET_OK;
+    GUARD_END
+}
+
+et_status et_batch_set_profiling(et_batch *b, int32_t on) {
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    b->profile = on != 0;
     return ET_OK;
 }
 

@@ -80,6 +80,12 @@ struct BatchRT {
     Ctl hctl{};
     cudaGraphExec_t gexec = nullptr;
     unsigned long long graph_key = 0;
+    // profiling
+    static constexpr int NSTAGE = 6;
+    bool profile = false, profiled_run = false;
+    cudaEvent_t ev[NSTAGE + 1] = {};
+    int kernel_launches = -1;
+    unsigned long long launches_key = 0;
 
     BatchRT(Ctx *c, const et_params &pp);
     ~BatchRT();
@@ -98,7 +104,9 @@ struct BatchRT {
     et_status fetch(int64_t *view_off, et_track *out, int64_t cap, int64_t *n_tracks, int32_t *mem,
                     int64_t mcap, int64_t *n_members);
     et_status seed_counts(int32_t *si, int32_t *sj, int32_t *cnt, int64_t cap, int64_t *n_seeds);
-    void stats(et_stats *o) const;
+    void stats(et_stats *o);
+    void mark(int stage, cudaStream_t st);
+    int count_kernels();
 };
 
 }  // namespace et

@@ -45,11 +45,15 @@ class Stats(C.Structure):
     _fields_ = [("n_grains", C.c_int64), ("n_seeds", C.c_int64), ("n_tests", C.c_int64),
                 ("n_hits", C.c_int64), ("n_candidates", C.c_int64), ("n_members", C.c_int64),
                 ("n_tracks", C.c_int64), ("n_track_members", C.c_int64), ("merge_rounds", C.c_int32),
-                ("cell", C.c_int32 * 3)]
+                ("cell", C.c_int32 * 3), ("kernel_launches", C.c_int32), ("profiled", C.c_int32),
+                ("stage_ms", C.c_float * 6)]
+
+    STAGES = ("cells", "seeds", "tube_count", "members", "merge", "output")
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "cell"}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("cell", "stage_ms")}
         d["cell"] = tuple(self.cell)
+        d["stage_ms"] = dict(zip(self.STAGES, (float(x) for x in self.stage_ms))) if self.profiled else None
         return d
 
 
@@ -97,6 +101,7 @@ _SIGS = {
                                    C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "et_batch_stats": (C.c_int32, [C.c_void_p, C.POINTER(Stats)]),
     "et_batch_sync": (C.c_int32, [C.c_void_p]),
+    "et_batch_set_profiling": (C.c_int32, [C.c_void_p, C.c_int32]),
     "et_batch_destroy": (C.c_int32, [C.c_void_p]),
     "et_server_create": (C.c_int32, [C.c_void_p, C.POINTER(Params), C.c_uint64, C.c_int32,
                                      C.POINTER(C.c_void_p)]),
@@ -274,6 +279,9 @@ class Batch:
 
     def sync(self):
         _check(lib().et_batch_sync(self._h))
+
+    def set_profiling(self, on=True):
+        _check(lib().et_batch_set_profiling(self._h, 1 if on else 0))
 
     def fetch(self):
         """(tracks, members, view_track_offsets)."""

@@ -53,7 +53,7 @@ def test_track_layout_matches_header():
     from paper_1311_5334_gb300 import et
     assert et.TRACK_DTYPE.itemsize == 56
     assert C.sizeof(et.Params) == 32
-    assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4
+    assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4 + 4 * 2 + 4 * 6
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
