@@ -248,6 +248,37 @@ et_status et_server_fetch(et_server *s, uint64_t tag, et_track *tracks, int64_t 
                           int64_t *n_members);
 et_status et_server_destroy(et_server *s);
 
+/* ------------------------------------------------------------------ no allocation */
+
+/* The paper has no counterpart to this entry point: it exists for callers
+ * that cannot call cudaMalloc -- an acquisition loop that must not block on
+ * the device-wide synchronisation an allocation can cause, code running in a
+ * host function enqueued on a stream (where CUDA calls are not allowed), or
+ * an application whose framework has already reserved the free device memory
+ * for its own pool.
+ *
+ * For each pair k (d_pairs[2k], d_pairs[2k+1]: indices into the view's grains)
+ * it writes to d_counts[k] the number of grains of the view within tube_r of
+ * the line through the two grains -- the same exact count et_view_seed_counts
+ * reports for a seed -- or -1 for a pair with an index outside [0, n) or two
+ * equal indices, and for every pair if a coordinate lies outside
+ * [0, extent).  d_xyz (int32 [n][3]), d_pairs (int32 [n_pairs][2]) and d_counts
+ * (int32 [n_pairs]) are DEVICE memory of the current device, owned by the
+ * caller; the work is enqueued on `stream` (NULL = legacy default stream) and
+ * the call returns without waiting.
+ *
+ * Nothing is allocated.  The intermediate cell list lives in one fixed
+ * array of about 3 MB (ET_NOALLOC_MAX_GRAINS grains, ET_NOALLOC_MAX_CELLS cells)
+ * that every GPU which loads the library keeps until the process exits.  The
+ * first call on a device looks up that array's device address; make it
+ * before any stream capture.  All calls share the array, so calls whose work
+ * overlaps on the GPU race: order them (one stream, or events).  Views larger
+ * than ET_NOALLOC_MAX_GRAINS are rejected with ET_ERR_INVALID_ARG. */
+#define ET_NOALLOC_MAX_GRAINS 65536
+#define ET_NOALLOC_MAX_CELLS 262144
+et_status et_tube_count_noalloc(const int32_t *d_xyz, int64_t n, const et_params *params,
+                                const int32_t *d_pairs, int64_t n_pairs, int32_t *d_counts, void *stream);
+
 /* ------------------------------------------------------------------ misc */
 
 const char *et_last_error(void);

@@ -111,6 +111,8 @@ _SIGS = {
     "et_server_fetch": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                                     C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "et_server_destroy": (C.c_int32, [C.c_void_p]),
+    "et_tube_count_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(Params), C.c_void_p, C.c_int64,
+                                          C.c_void_p, C.c_void_p]),
 }
 
 
@@ -396,6 +398,18 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def tube_count_noalloc(d_xyz, params, d_pairs, d_counts, stream=None):
+    """et_tube_count_noalloc on CUDA tensors: d_xyz (n, 3) int32, d_pairs (m, 2)
+    int32, d_counts (m,) int32 output; allocates nothing, returns immediately."""
+    p = _params(params)
+    for t in (d_xyz, d_pairs, d_counts):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("device tensors must be contiguous CUDA tensors")
+    _check(lib().et_tube_count_noalloc(C.c_void_p(d_xyz.data_ptr()), d_xyz.shape[0], C.byref(p),
+                                       C.c_void_p(d_pairs.data_ptr()), d_pairs.shape[0],
+                                       C.c_void_p(d_counts.data_ptr()), _stream_ptr(stream)))
 
 
 def track_tuples(tracks, members):
