@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 
 from paper_1311_5334_gb300 import synth  # noqa: E402
 
-VIEW_CM2 = 300e-4 * 300e-4          # one 300 x 300 um view in cm^2
+VIEW_CM2 = 300e-4 * 300e-4          # one 300 x 300 um view in cm^2 (stress views: 1000 x 1000 um)
 WORKLOAD = ("batched: 256 views 300x300x50 um, fog lognormal (median 10k, sigma 0.6, 2k-50k), "
             "isotropic through-going tracks at 1% of the fog count, gaps 3.3 um, jitter 0.05/0.3 um, "
             "int32 10 nm coords, seed window 5-20 um, tube 0.4 um, min hits 8, seed 3")
@@ -113,6 +113,9 @@ WORKLOADS = {
               "seed window 5-20 um, tube 0.4 um, min hits 8, seed 2"),
     "pr1": ("PR1: one view 300x300x50 um, 2,000 fog + 20 isotropic tracks (gaps 3.3 um), jitter 0.05/0.3 um, "
             "int32 10 nm coords, seed window 5-20 um, tube 0.4 um, min hits 8, seed 1"),
+    "stress": ("stress: one view 1000x1000x50 um, 1,000,000 fog + 5,000 isotropic tracks (20% short-range, "
+               "gaps 1.6 um; through-going gaps 3.3 um), jitter 0.05/0.3 um, int32 10 nm coords, "
+               "seed window 5-20 um, tube 0.4 um, min hits 8, seed 5"),
 }
 
 
@@ -121,6 +124,8 @@ def make_workload(name="batched"):
         views = [synth.dense()]
     elif name == "pr1":
         views = [synth.pr1()]
+    elif name == "stress":
+        views = [synth.stress()]
     else:
         views = synth.batched(n_views=256, seed=3)
     xyz, offs = synth.concat(views)
@@ -278,11 +283,13 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "views_per_step": n_views,
                        "grains_per_step": int(offs[-1]),
                        "seeds_per_step": ref_stats["n_seeds"], "tube_tests_per_step": ref_stats["n_tests"],
-                       "tracks_per_step": ref_stats["n_tracks"], "cell_units": list(ref_stats["cell"]),
+                       "tracks_per_step": ref_stats["n_tracks"], "candidates_per_step": ref_stats["n_candidates"],
+                       "candidate_members_per_step": ref_stats["n_members"],
+                       "merge_rounds": ref_stats["merge_rounds"], "cell_units": list(ref_stats["cell"]),
                        "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
                        "parallelism": f"replicas: one {n_views}-view batch per rank x {ws}"},
             "seeds_per_s": seeds_per_s,
-            "cm2_per_h": value * VIEW_CM2 * 3600,
+            "cm2_per_h": value * (1e-4 if args.workload == "stress" else VIEW_CM2) * 3600,
             "plain_views_per_s": plain_views_per_s,
             "stage_ms": stage_ms,
             "wall_s": wall,

@@ -90,9 +90,11 @@ typedef struct {
 } et_tuning;
 
 /* One reconstructed track.  seed_i / seed_j are indices into the caller's grain
- * array of the view (seed_i is the lower-rank grain).  member_offset indexes
- * the member array returned with it; members of one track are ascending grain
- * indices of the view. */
+ * array of the view (seed_i is the lower-rank grain).  count is the seed's tube
+ * count (all grains along its line, the candidate's rank key); nhits <= count
+ * is the number of grains the track owns after exclusive association.
+ * member_offset indexes the member array returned with it; members of one
+ * track are ascending grain indices of the view. */
 typedef struct {
     int32_t seed_i, seed_j;
     int32_t nhits;
@@ -101,6 +103,8 @@ typedef struct {
     float c[3];
     float u[3];
     float tmin, tmax;
+    int32_t count;
+    int32_t reserved;
 } et_track;
 
 /* Counters of the last completed run. */

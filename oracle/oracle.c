@@ -250,7 +250,23 @@ static seed_rec *all_seeds(const or_ctx *c, int64_t *n_out) {
 
 int64_t or_seed_total(const or_ctx *c) {
     int64_t total = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : total)
+#endif
     for (int64_t a = 0; a < c->n; ++a) total += seeds_of(c, (int32_t)a, NULL, 0);
+    return total;
+}
+
+/* Number of seeds whose lo grain is each grain (input ids); returns the total. */
+int64_t or_seeds_per_grain(const or_ctx *c, int64_t *out) {
+    int64_t total = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1024) reduction(+ : total)
+#endif
+    for (int64_t a = 0; a < c->n; ++a) {
+        out[a] = seeds_of(c, (int32_t)a, NULL, 0);
+        total += out[a];
+    }
     return total;
 }
 

@@ -82,6 +82,8 @@ def lib():
             L.or_rank.argtypes = [C.c_void_p, C.c_int32]
             L.or_seed_total.restype = C.c_int64
             L.or_seed_total.argtypes = [C.c_void_p]
+            L.or_seeds_per_grain.restype = C.c_int64
+            L.or_seeds_per_grain.argtypes = [C.c_void_p, P64]
             L.or_list_seeds.restype = C.c_int64
             L.or_list_seeds.argtypes = [C.c_void_p, P32, P32, C.c_int64]
             L.or_count_pairs.argtypes = [C.c_void_p, P32, P32, C.c_int64, P32, C.c_int]
@@ -170,6 +172,12 @@ class Oracle:
     def ranks(self):
         L = lib()
         return np.array([L.or_rank(self._h, i) for i in range(self.n)], dtype=np.int64)
+
+    def seeds_per_grain(self):
+        """Seeds per lo grain (input ids), int64 array of length n."""
+        out = np.zeros(max(self.n, 1), dtype=np.int64)
+        lib().or_seeds_per_grain(self._h, out.ctypes.data_as(C.POINTER(C.c_int64)))
+        return out[:self.n]
 
     def seeds(self):
         """All seeds (lo, hi) as input ids, lo = lower rank, ordered by (rank lo, rank hi)."""

@@ -33,8 +33,9 @@ struct TrackOut {
     int seed_i, seed_j, nhits, view;
     long long member_offset;
     float c[3], u[3], tmin, tmax;
+    int count, reserved;
 };
-static_assert(sizeof(TrackOut) == 56, "et_track layout");
+static_assert(sizeof(TrackOut) == 64, "et_track layout");
 
 namespace {
 
@@ -343,6 +344,8 @@ __global__ void k_fit(Batch b, Work w, Out o) {
             r.u[0] = u[0]; r.u[1] = u[1]; r.u[2] = u[2];
             r.tmin = tmin;
             r.tmax = tmax;
+            r.count = (int)w.c_cnt[c];
+            r.reserved = 0;
             tracks[t] = r;
         }
     }

@@ -65,8 +65,8 @@ class Result(C.Structure):
 
 TRACK_DTYPE = np.dtype([("seed_i", "<i4"), ("seed_j", "<i4"), ("nhits", "<i4"), ("view", "<i4"),
                         ("member_offset", "<i8"), ("c", "<f4", (3,)), ("u", "<f4", (3,)),
-                        ("tmin", "<f4"), ("tmax", "<f4")])
-assert TRACK_DTYPE.itemsize == 56
+                        ("tmin", "<f4"), ("tmax", "<f4"), ("count", "<i4"), ("reserved", "<i4")])
+assert TRACK_DTYPE.itemsize == 64
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)

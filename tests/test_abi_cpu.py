@@ -51,7 +51,7 @@ def test_abi_version_and_status_strings(libet):
 
 def test_track_layout_matches_header():
     from paper_1311_5334_gb300 import et
-    assert et.TRACK_DTYPE.itemsize == 56
+    assert et.TRACK_DTYPE.itemsize == 64
     assert C.sizeof(et.Params) == 32
     assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4 + 4 * 2 + 4 * 6
 

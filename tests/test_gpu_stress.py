@@ -1,0 +1,112 @@
+"""The stress workload (one 1000x1000x50 um view, ~1.23 M grains, ~4.2e8 seed
+hypotheses) at full size, in the launch configuration bench.py times.
+
+The oracle cannot evaluate the whole method at this size in test time, so the
+CUDA result is checked through properties that hold at any size plus exact
+sampled comparisons:
+  * seeds: the number of seeds of every lo grain equals the oracle's, and
+    sampled seed records satisfy the window and orientation and carry the
+    oracle's exact count;
+  * candidates: their number equals the records with count >= min_hits;
+  * tracks: owned members are disjoint and >= min_hits per track; for sampled
+    tracks the tube count equals the oracle's, the members lie in the tube,
+    and every tube grain a track does not own is owned by an earlier track;
+  * sampled candidates that were not accepted keep fewer than min_hits
+    grains not owned by tracks that come before them in candidate order.
+"""
+import numpy as np
+import pytest
+
+from paper_1311_5334_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def stress_run(oracle_mod):
+    from paper_1311_5334_gb300 import et
+    v = synth.stress()
+    p = synth.params(v.extent)
+    with et.Context(0) as ctx:
+        view = ctx.view(v.xyz, p)
+        view.find()
+        tracks, members = view.fetch()
+        st = view.stats()
+        si, sj, sc = view.seed_counts()
+        view.close()
+    o = oracle_mod.Oracle(v.xyz, v.extent, p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"])
+    yield v, p, tracks, members, st, (si, sj, sc), o
+    o.close()
+
+
+def test_stress_seeds(stress_run):
+    v, p, tracks, members, st, (si, sj, sc), o = stress_run
+    per = o.seeds_per_grain()
+    assert st["n_seeds"] == int(per.sum()) == len(si)
+    assert np.array_equal(np.bincount(si, minlength=v.n), per)
+    rng = np.random.default_rng(55)
+    idx = rng.choice(len(si), size=3000, replace=False)
+    a, b = v.xyz[si[idx]].astype(np.int64), v.xyz[sj[idx]].astype(np.int64)
+    d2 = ((b - a) ** 2).sum(axis=1)
+    assert np.all((d2 >= p["seed_min"] ** 2) & (d2 < p["seed_max"] ** 2))
+    lex_lt = [tuple(x) < tuple(y) for x, y in zip(a, b)]
+    assert all(lex_lt)
+    assert np.array_equal(o.count_pairs(si[idx], sj[idx]), sc[idx])
+    assert st["n_candidates"] == int((sc >= p["min_hits"]).sum())
+    assert st["n_hits"] == int(sc.astype(np.int64).sum())
+
+
+def _ranks(xyz):
+    order = np.lexsort((xyz[:, 2], xyz[:, 1], xyz[:, 0]))
+    r = np.empty(len(xyz), dtype=np.int64)
+    r[order] = np.arange(len(xyz))
+    return r
+
+
+def test_stress_tracks_follow_the_greedy_rule(stress_run):
+    v, p, tracks, members, st, (si, sj, sc), o = stress_run
+    H = p["min_hits"]
+    nt = len(tracks)
+    assert nt == st["n_tracks"] > 1000
+    assert np.all(tracks["nhits"] >= H) and np.all(tracks["count"] >= tracks["nhits"])
+    off = tracks["member_offset"].astype(np.int64)
+    assert np.array_equal(off, np.concatenate([[0], np.cumsum(tracks["nhits"].astype(np.int64))[:-1]]))
+    assert len(members) == int(tracks["nhits"].astype(np.int64).sum())
+    tid = np.repeat(np.arange(nt), tracks["nhits"])
+    assert np.bincount(members, minlength=v.n).max() == 1, "a grain is owned by two tracks"
+    inner = np.ones(len(members), dtype=bool)
+    inner[off] = False                      # first member of each track
+    assert np.all(np.diff(members)[inner[1:]] > 0), "members not ascending within a track"
+    owner = np.full(v.n, -1, dtype=np.int64)
+    owner[members] = tid
+    rank = _ranks(v.xyz)
+    # candidate keys of the tracks, ascending in acceptance order
+    keys = np.stack([-tracks["count"].astype(np.int64), rank[tracks["seed_i"]], rank[tracks["seed_j"]]], 1)
+
+    def less(k, c):
+        return (k[:, 0] < c[0]) | ((k[:, 0] == c[0]) & ((k[:, 1] < c[1]) | ((k[:, 1] == c[1]) & (k[:, 2] < c[2]))))
+
+    k0, k1 = keys[:-1], keys[1:]
+    ordered = (k0[:, 0] < k1[:, 0]) | ((k0[:, 0] == k1[:, 0]) &
+                                       ((k0[:, 1] < k1[:, 1]) | ((k0[:, 1] == k1[:, 1]) & (k0[:, 2] < k1[:, 2]))))
+    assert np.all(ordered), "tracks not in candidate order"
+    rng = np.random.default_rng(56)
+    for t in rng.choice(nt, size=200, replace=False):
+        tube = o.tube_members(tracks["seed_i"][t], tracks["seed_j"][t])
+        assert len(tube) == tracks["count"][t]
+        mine = tube[owner[tube] == t]
+        assert len(mine) == tracks["nhits"][t]
+        others = owner[tube[owner[tube] != t]]
+        assert np.all((others >= 0) & (others < t)), "a free grain or a later owner inside the tube"
+    # sampled candidates that are not tracks
+    accepted = set(zip(tracks["seed_i"].tolist(), tracks["seed_j"].tolist()))
+    cand = np.nonzero(sc >= H)[0]
+    for k in rng.choice(cand, size=min(500, len(cand)), replace=False):
+        a, b = int(si[k]), int(sj[k])
+        if (a, b) in accepted:
+            continue
+        key = (-int(sc[k]), int(rank[a]), int(rank[b]))
+        before = int(less(keys, key).sum())
+        tube = o.tube_members(a, b)
+        free = tube[(owner[tube] < 0) | (owner[tube] >= before)]
+        assert len(free) < H, (a, b, len(free))

@@ -254,6 +254,16 @@ def test_hash_cover_equals_all_grains_pr1(oracle_mod, cell):
     assert np.array_equal(a, b)
 
 
+def test_seeds_per_grain_matches_seed_list(oracle_mod):
+    from paper_1311_5334_gb300 import synth
+    v = synth.pr1()
+    with _oracle(oracle_mod, v.xyz, v.extent, 500, 2000, 40, 8) as o:
+        lo, hi = o.seeds()
+        per = o.seeds_per_grain()
+    assert per.sum() == len(lo)
+    assert np.array_equal(per, np.bincount(lo, minlength=v.n))
+
+
 def test_hash_cover_equals_all_grains_lattice(oracle_mod):
     """A regular lattice makes many seeds axis-aligned or diagonal, with grains
     exactly on tube walls and cell faces."""
