@@ -220,9 +220,13 @@ def run_ours(args):
 
     batch = et.Batch(ctx, params)
     batch.set_profiling(True)
+    tuned = None
     if args.cell:
         batch.set_tuning(tuple(int(c) for c in args.cell.split(",")))
     batch.load(xyz_d, offs, stream=stream)
+    if not args.cell:
+        cell, ms = batch.autotune(stream=stream)
+        tuned = {"cell": list(cell), "ms_per_run": ms, "how": "et_batch_autotune: fastest of 8 cell shapes"}
 
     def step():
         batch.load(xyz_d, offs, stream=stream)
@@ -286,6 +290,7 @@ def run_ours(args):
                        "tracks_per_step": ref_stats["n_tracks"], "candidates_per_step": ref_stats["n_candidates"],
                        "candidate_members_per_step": ref_stats["n_members"],
                        "merge_rounds": ref_stats["merge_rounds"], "cell_units": list(ref_stats["cell"]),
+                       "autotune": tuned,
                        "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
                        "parallelism": f"replicas: one {n_views}-view batch per rank x {ws}"},
             "seeds_per_s": seeds_per_s,
@@ -302,6 +307,10 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(ref_stats["kernel_launches"]) * args.steps,
             "clocks": clk}
+    if not args.no_extra and args.workload == "batched":
+        rate, nv = args.served_rate, args.served_views
+        line["served"] = served_run(ctx, params, views, rate, nv)
+        line["served"]["pool"] = f"arrivals cycle over the {n_views} batched views; 20 GB budget"
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra:
         budget = float(os.environ.get("ET_CPU_BASELINE_S", "15"))
@@ -317,6 +326,42 @@ def run_ours(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batch=256, seed=4):
+    """Poisson arrivals at `rate` views/s through et_server_submit / et_server_poll.
+
+    Latency of a view = result ready - its scheduled arrival (CLOCK_MONOTONIC on
+    both sides), so a producer that falls behind does not hide queueing."""
+    from paper_1311_5334_gb300 import et
+    arrivals = synth.poisson_arrivals(n_views, rate, seed=seed)
+    done = {}
+    with ctx.server(params, budget_bytes, max_batch_views=max_batch) as srv:
+        t0 = time.monotonic_ns() + 20_000_000
+        sched = t0 + (arrivals * 1e9).astype(np.int64)
+        busy = [0]
+
+        def producer():
+            for i in range(n_views):
+                wait = int(sched[i]) - time.monotonic_ns()
+                if wait > 0:
+                    time.sleep(wait / 1e9)
+                while srv.submit(pool[i % len(pool)].xyz, tag=i) == et.BUSY:
+                    busy[0] += 1
+                    time.sleep(1e-4)
+
+        th = threading.Thread(target=producer, daemon=True)
+        th.start()
+        while len(done) < n_views:
+            for r in srv.poll(max_results=1024, timeout_us=50_000):
+                if r.status != et.OK:
+                    raise RuntimeError(f"served view {r.tag} failed with status {r.status}")
+                done[int(r.tag)] = int(r.t_done_ns)
+        th.join()
+    lat = np.array([(done[i] - sched[i]) / 1e6 for i in range(n_views)])
+    span = (max(done.values()) - t0) / 1e9
+    return {"rate_per_s": rate, "views": n_views, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "views_per_s": n_views / span, "busy_retries": busy[0]}
 
 
 def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws):
@@ -377,12 +422,37 @@ def main():
                     help="time only the device-resident step (no plain/e2e/cpu baseline); for profilers")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched")
     ap.add_argument("--cell", default="", help="cell edges x,y,z in coordinate units (default: automatic)")
+    ap.add_argument("--served-rate", type=float, default=1000.0, help="Poisson rate of the served run (views/s)")
+    ap.add_argument("--served-views", type=int, default=3000, help="views in the served run")
+    ap.add_argument("--served-sweep", action="store_true",
+                    help="only the served form: rates 100..5000 views/s over 10,000 views (seed 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.served_sweep:
+        return run_served_sweep(args)
     return run_ours(args)
+
+
+def run_served_sweep(args):
+    """The served configuration: 10,000 views (size law of the batched views,
+    seed 4) arriving as a Poisson process, rate swept 100-5,000 views/s, under a
+    20 GB device-memory budget.  One JSON line per rate."""
+    import torch
+    from paper_1311_5334_gb300 import et
+    torch.cuda.set_device(0)
+    pool = synth.batched(n_views=512, seed=4)
+    params = synth.params(pool[0].extent)
+    with et.Context(0) as ctx:
+        for rate in (100, 200, 500, 1000, 2000, 5000):
+            n = min(args.served_views if args.served_views != 3000 else 10000, 10000)
+            r = served_run(ctx, params, pool, rate, n)
+            r.update({"metric": "served view latency", "pool": "512 distinct views (seed 4) cycled",
+                      "budget_bytes": 20 << 30})
+            print(json.dumps(r), flush=True)
+    return 0
 
 
 if __name__ == "__main__":

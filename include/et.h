@@ -202,6 +202,13 @@ et_status et_batch_create(et_ctx *ctx, const et_params *params, et_batch **out);
 et_status et_batch_load(et_batch *b, const int32_t *xyz, const int64_t *offsets, int32_t n_views,
                         int32_t on_device, void *stream);
 et_status et_batch_set_tuning(et_batch *b, const et_tuning *tuning);
+/* Picks the cell-list shape for the loaded batch by timing the whole path on
+ * it: up to max_trials candidate shapes derived from the batch's mean grain
+ * density (cubic and anisotropic, rows along x kept short), two runs each,
+ * CUDA-event timed; the fastest is kept as the batch's tuning and returned in
+ * *chosen (may be NULL), its time per run in *best_ms (may be NULL).
+ * Synchronous.  Results never depend on the choice, only the speed does. */
+et_status et_batch_autotune(et_batch *b, void *stream, int32_t max_trials, et_tuning *chosen, float *best_ms);
 /* Enqueues the path for all loaded views.  use_graph != 0 captures the launch
  * sequence once per batch shape and replays it. */
 et_status et_batch_find(et_batch *b, void *stream, int32_t use_graph);

@@ -42,6 +42,8 @@ struct Ctl {
     u32 bar_gen;        // grid barrier generation
     u32 active[2];      // merge: participants per round (ping-pong)
     u32 pad[2];
+    u64 ncl[2];         // merge: lengths of the undecided-candidate lists (ping-pong)
+    u32 round_active[64];   // merge: participants of the first 64 rounds (diagnostics)
 };
 
 // Everything a kernel needs to know about the batch.  Passed by value.
@@ -86,6 +88,7 @@ struct Work {
     // merge
     u64 *best[2];        // per grain
     int *owner;          // per grain: accepting candidate or -1
+    int *clist[2];       // undecided candidates carried to the next round (cand_cap each)
     // diagnostic per-seed record (optional)
     int *rec_lo, *rec_hi, *rec_cnt;
     u64 rec_cap;

@@ -74,17 +74,17 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
     }
 }
 
-// Tube counts with warp-level load balancing.
+// Tube walks with warp-level load balancing (tube counts and member lists).
 //
-// A warp takes 32 seeds (one per lane).  Each seed's cover is split into work
+// A warp takes 32 lines (one per lane).  Each line's cover is split into work
 // items: the slabs of cells along whichever of y or z the line crosses more
 // cells of ("outer" axis).  Within one slab the tube meets only 1-3 rows of
 // the other ("inner") axis, each row a run of x cells that is one contiguous
 // range of the cell-ordered grains, so items cost about the same.  The items
-// of the 32 seeds are dealt to the lanes in rounds of 32: a lane finds the
-// seed owning its item from the start positions of the seeds that begin in
-// the round (an OR-reduction of one-hot masks and a popcount).  Seed geometry
-// is resolved once into shared memory; hit counts are merged with
+// of the 32 lines are dealt to the lanes in rounds of 32: a lane finds the
+// line owning its item from the start positions of the lines that begin in
+// the round (an OR-reduction of one-hot masks and a popcount).  Line geometry
+// is resolved once into shared memory; per-line results are merged with
 // shared-memory atomics.  The geometry is the conservative cover of
 // tube_cover() (tube.cuh), with the per-slab terms hoisted.
 constexpr int TW = 8;   // warps per block
@@ -101,6 +101,127 @@ struct SeedSm {
     u32 cs_off;                      // view offset in cell_start
 };
 
+// Resolves the cover geometry of the line through ga and gb into q and
+// returns its number of items (outer slabs).
+__device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int view, SeedSm &q) {
+    const float pad = (float)b.r + COVER_PAD;
+    const int ny = b.nc[1], nz = b.nc[2], nx = b.nc[0];
+    q.ax = ga.x; q.ay = ga.y; q.az = ga.z;
+    q.wx = gb.x - ga.x; q.wy = gb.y - ga.y; q.wz = gb.z - ga.z;
+    q.R = b.r2 * ((long long)q.wx * q.wx + (long long)q.wy * q.wy + (long long)q.wz * q.wz);
+    q.cs_off = (u32)view * (u32)b.ncell;
+    const float ax = (float)q.ax, ay = (float)q.ay, az = (float)q.az;
+    const float wx = (float)q.wx, wy = (float)q.wy, wz = (float)q.wz;
+    const float iwx = q.wx ? 1.0f / wx : 0.0f;
+    const float iwy = q.wy ? 1.0f / wy : 0.0f;
+    const float iwz = q.wz ? 1.0f / wz : 0.0f;
+    float t0 = -3.0e38f, t1 = 3.0e38f;
+    if (q.wx) {
+        float ta = (-pad - ax) * iwx, tb = ((float)(b.ext[0] - 1) + pad - ax) * iwx;
+        t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    if (q.wy) {
+        float ta = (-pad - ay) * iwy, tb = ((float)(b.ext[1] - 1) + pad - ay) * iwy;
+        t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    if (q.wz) {
+        float ta = (-pad - az) * iwz, tb = ((float)(b.ext[2] - 1) + pad - az) * iwz;
+        t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
+    }
+    q.t0 = t0;
+    q.t1 = t1;
+    q.xl0 = ax - pad;
+    q.xh0 = ax + pad;
+    q.fwx = wx;
+    const float yl = ay + fminf(t0 * wy, t1 * wy) - pad, yh = ay + fmaxf(t0 * wy, t1 * wy) + pad;
+    const float zl = az + fminf(t0 * wz, t1 * wz) - pad, zh = az + fmaxf(t0 * wz, t1 * wz) + pad;
+    const int cy0 = max(0, floor_i(yl * b.ics[1])), cy1 = min(ny - 1, floor_i(yh * b.ics[1]));
+    const int cz0 = max(0, floor_i(zl * b.ics[2])), cz1 = min(nz - 1, floor_i(zh * b.ics[2]));
+    const int nyc = max(0, cy1 - cy0 + 1), nzc = max(0, cz1 - cz0 + 1);
+    const float csy = (float)b.cs[1], csz = (float)b.cs[2];
+    if (nyc >= nzc) {   // outer y, inner z; row = (cz * ny + cy) * nx
+        q.ao = ay; q.wo = wy; q.iwo = iwy; q.cso = csy;
+        q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.ics[2]; q.nci = nz;
+        q.mo = nx; q.mi = ny * nx;
+        q.o0 = cy0;
+        return nyc;
+    }
+    // outer z, inner y
+    q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
+    q.ai = ay; q.wi = wy; q.iwi = iwy; q.csi = csy; q.ici = b.ics[1]; q.nci = ny;
+    q.mo = ny * nx; q.mi = nx;
+    q.o0 = cz0;
+    return nzc;
+}
+
+// Deals the items of the 32 lines in sp to the lanes of the warp and calls
+// f(owner_lane, qq, beg, end) for every row range of every item.  n_items is
+// this lane's own line's item count (0 for an idle lane).
+template <class F>
+__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, F &&f) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_le = 0xffffffffu >> (31 - lane);
+    const float pad = (float)b.r + COVER_PAD;
+    const int nx = b.nc[0];
+    const float icsx = b.ics[0];
+    int incl = n_items;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int excl = incl - n_items;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (n_items > 0) sp[lane].excl = excl;
+    __syncwarp();
+    for (int ibase = 0; ibase < total; ibase += 32) {
+        // lines whose first item falls in this round mark its position;
+        // a lane's owner is the last line started at or before it
+        const bool starts = n_items > 0 && excl >= ibase && excl < ibase + 32;
+        const unsigned smask = __reduce_or_sync(0xffffffffu, starts ? (1u << (excl - ibase)) : 0u);
+        const int before = __popc(__ballot_sync(0xffffffffu, n_items > 0 && excl < ibase));
+        const int own = before + __popc(smask & lane_le) - 1;
+        const int item = ibase + lane;
+        if (item >= total) continue;
+        const SeedSm &qq = sp[own];
+        const int co = qq.o0 + (item - qq.excl);
+        float ta = qq.t0, tb = qq.t1;
+        const float wo = qq.wo;
+        if (wo != 0.0f) {
+            const float cso = qq.cso, ao = qq.ao, iwo = qq.iwo;
+            const float u0 = ((float)co * cso - pad - ao) * iwo;
+            const float u1 = ((float)co * cso + cso - 1.0f + pad - ao) * iwo;
+            ta = fmaxf(ta, fminf(u0, u1));
+            tb = fminf(tb, fmaxf(u0, u1));
+        }
+        if (ta > tb) continue;
+        const float ai = qq.ai, wi = qq.wi, iwi = qq.iwi, csi = qq.csi;
+        const float il = ai + fminf(ta * wi, tb * wi) - pad;
+        const float ih = ai + fmaxf(ta * wi, tb * wi) + pad;
+        const int ci0 = max(0, floor_i(il * qq.ici)), ci1 = min(qq.nci - 1, floor_i(ih * qq.ici));
+        // inner slab ci spans t in [vb + ci*vs, vb + ci*vs + vw] (ordered by the sign of w)
+        const float vs = csi * iwi, vb = (-pad - ai) * iwi, vw = (csi - 1.0f + 2.0f * pad) * iwi;
+        const float xl0 = qq.xl0, xh0 = qq.xh0, fwx = qq.fwx;
+        const int rowo = co * qq.mo, mi = qq.mi;
+        const u32 *__restrict__ cs = b.cell_start + qq.cs_off;
+        for (int ci = ci0; ci <= ci1; ++ci) {
+            float za = ta, zb = tb;
+            if (wi != 0.0f) {
+                const float v0 = vb + (float)ci * vs, v1 = v0 + vw;
+                za = fmaxf(za, fminf(v0, v1));
+                zb = fminf(zb, fmaxf(v0, v1));
+                if (za > zb) continue;
+            }
+            const float pa = za * fwx, pb = zb * fwx;
+            const int cx0 = max(0, floor_i((xl0 + fminf(pa, pb)) * icsx));
+            const int cx1 = min(nx - 1, floor_i((xh0 + fmaxf(pa, pb)) * icsx));
+            if (cx0 > cx1) continue;
+            const int row = rowo + ci * mi;
+            f(own, qq, cs[row + cx0], cs[row + cx1 + 1]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int record) {
     if (input_failed(b.ctl)) return;
     const u64 ns = b.ctl->n_seeds;
@@ -111,13 +232,8 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     __shared__ SeedSm sp[TW][32];
     __shared__ u32 scount[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const unsigned lane_le = 0xffffffffu >> (31 - lane);
     const u64 nwarps = (u64)gridDim.x * TW;
-    const float pad = (float)b.r + COVER_PAD;
-    const int nx = b.nc[0], ny = b.nc[1], nz = b.nc[2];
-    const float icsx = b.ics[0];
     const int4 *__restrict__ gc = b.gc;
-    const u32 *__restrict__ cell_start = b.cell_start;
     u64 tests = 0, hits = 0;
     for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < ns; base += nwarps * 32) {
         const u64 s = base + lane;
@@ -125,130 +241,30 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         int lo = 0, hi = 0, n_items = 0;
         int cw = 0, cv = 0;
         if (valid) {
-            SeedSm q;
             const int2 sd = w.seeds[s];
             lo = sd.x;
             hi = sd.y;
             const int4 ga = b.gr[lo], gb = b.gr[hi];
             cw = ga.w;
             cv = gb.w;
-            q.ax = ga.x; q.ay = ga.y; q.az = ga.z;
-            q.wx = gb.x - ga.x; q.wy = gb.y - ga.y; q.wz = gb.z - ga.z;
-            q.R = b.r2 * ((long long)q.wx * q.wx + (long long)q.wy * q.wy + (long long)q.wz * q.wz);
-            q.cs_off = (u32)view_of(b.goff, b.V, lo) * (u32)b.ncell;
-            const float ax = (float)q.ax, ay = (float)q.ay, az = (float)q.az;
-            const float wx = (float)q.wx, wy = (float)q.wy, wz = (float)q.wz;
-            const float iwx = q.wx ? 1.0f / wx : 0.0f;
-            const float iwy = q.wy ? 1.0f / wy : 0.0f;
-            const float iwz = q.wz ? 1.0f / wz : 0.0f;
-            float t0 = -3.0e38f, t1 = 3.0e38f;
-            if (q.wx) {
-                float ta = (-pad - ax) * iwx, tb = ((float)(b.ext[0] - 1) + pad - ax) * iwx;
-                t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
-            }
-            if (q.wy) {
-                float ta = (-pad - ay) * iwy, tb = ((float)(b.ext[1] - 1) + pad - ay) * iwy;
-                t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
-            }
-            if (q.wz) {
-                float ta = (-pad - az) * iwz, tb = ((float)(b.ext[2] - 1) + pad - az) * iwz;
-                t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
-            }
-            q.t0 = t0;
-            q.t1 = t1;
-            q.xl0 = ax - pad;
-            q.xh0 = ax + pad;
-            q.fwx = wx;
-            const float yl = ay + fminf(t0 * wy, t1 * wy) - pad, yh = ay + fmaxf(t0 * wy, t1 * wy) + pad;
-            const float zl = az + fminf(t0 * wz, t1 * wz) - pad, zh = az + fmaxf(t0 * wz, t1 * wz) + pad;
-            const int cy0 = max(0, floor_i(yl * b.ics[1])), cy1 = min(ny - 1, floor_i(yh * b.ics[1]));
-            const int cz0 = max(0, floor_i(zl * b.ics[2])), cz1 = min(nz - 1, floor_i(zh * b.ics[2]));
-            const int nyc = max(0, cy1 - cy0 + 1), nzc = max(0, cz1 - cz0 + 1);
-            const float csy = (float)b.cs[1], csz = (float)b.cs[2];
-            if (nyc >= nzc) {   // outer y, inner z; row = (cz * ny + cy) * nx
-                q.ao = ay; q.wo = wy; q.iwo = iwy; q.cso = csy;
-                q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.ics[2]; q.nci = nz;
-                q.mo = nx; q.mi = ny * nx;
-                q.o0 = cy0; n_items = nyc;
-            } else {            // outer z, inner y
-                q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
-                q.ai = ay; q.wi = wy; q.iwi = iwy; q.csi = csy; q.ici = b.ics[1]; q.nci = ny;
-                q.mo = ny * nx; q.mi = nx;
-                q.o0 = cz0; n_items = nzc;
-            }
+            SeedSm q;
+            n_items = seed_setup(b, ga, gb, view_of(b.goff, b.V, lo), q);
             sp[wib][lane] = q;
         }
         scount[wib][lane] = 0;
-        int incl = n_items;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int excl = incl - n_items;
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (valid) sp[wib][lane].excl = excl;
-        __syncwarp();
-        for (int ibase = 0; ibase < total; ibase += 32) {
-            // seeds whose first item falls in this round mark its position;
-            // a lane's owner is the last seed started at or before it
-            const bool starts = n_items > 0 && excl >= ibase && excl < ibase + 32;
-            const unsigned smask = __reduce_or_sync(0xffffffffu, starts ? (1u << (excl - ibase)) : 0u);
-            const int before = __popc(__ballot_sync(0xffffffffu, n_items > 0 && excl < ibase));
-            const int c = __popc(smask & lane_le);
-            const int own = before + c - 1;
-            const int item = ibase + lane;
-            if (item >= total) continue;
-            const SeedSm &qq = sp[wib][own];
-            const int co = qq.o0 + (item - qq.excl);
-            float ta = qq.t0, tb = qq.t1;
-            const float wo = qq.wo;
-            if (wo != 0.0f) {
-                const float cso = qq.cso, ao = qq.ao, iwo = qq.iwo;
-                const float u0 = ((float)co * cso - pad - ao) * iwo;
-                const float u1 = ((float)co * cso + cso - 1.0f + pad - ao) * iwo;
-                ta = fmaxf(ta, fminf(u0, u1));
-                tb = fminf(tb, fmaxf(u0, u1));
-            }
-            if (ta > tb) continue;
-            const float ai = qq.ai, wi = qq.wi, iwi = qq.iwi, csi = qq.csi;
-            const float il = ai + fminf(ta * wi, tb * wi) - pad;
-            const float ih = ai + fmaxf(ta * wi, tb * wi) + pad;
-            const int ci0 = max(0, floor_i(il * qq.ici)), ci1 = min(qq.nci - 1, floor_i(ih * qq.ici));
-            // inner slab ci spans t in [vb + ci*vs, vb + ci*vs + vw] (ordered by the sign of w)
-            const float vs = csi * iwi, vb = (-pad - ai) * iwi, vw = (csi - 1.0f + 2.0f * pad) * iwi;
-            const float xl0 = qq.xl0, xh0 = qq.xh0, fwx = qq.fwx;
-            const int mo = qq.mo, mi = qq.mi;
-            const u32 *__restrict__ cs = cell_start + qq.cs_off;
+        warp_items(b, sp[wib], n_items, [&](int own, const SeedSm &qq, u32 k, u32 end) {
             const int3 a = make_int3(qq.ax, qq.ay, qq.az);
             const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
             const long long R = qq.R;
-            const int rowo = co * mo;
+            tests += end - k;
             u32 cnt = 0;
-            for (int ci = ci0; ci <= ci1; ++ci) {
-                float za = ta, zb = tb;
-                if (wi != 0.0f) {
-                    const float v0 = vb + (float)ci * vs, v1 = v0 + vw;
-                    za = fmaxf(za, fminf(v0, v1));
-                    zb = fminf(zb, fmaxf(v0, v1));
-                    if (za > zb) continue;
-                }
-                const float pa = za * fwx, pb = zb * fwx;
-                const int cx0 = max(0, floor_i((xl0 + fminf(pa, pb)) * icsx));
-                const int cx1 = min(nx - 1, floor_i((xh0 + fmaxf(pa, pb)) * icsx));
-                if (cx0 > cx1) continue;
-                const int row = rowo + ci * mi;
-                u32 k = cs[row + cx0];
-                const u32 end = cs[row + cx1 + 1];
-                tests += end - k;
-                for (; k + 1 < end; k += 2) {
-                    const int4 g0 = gc[k], g1 = gc[k + 1];
-                    cnt += in_tube(g0, a, d, R) + in_tube(g1, a, d, R);
-                }
-                if (k < end) cnt += in_tube(gc[k], a, d, R);
+            for (; k + 1 < end; k += 2) {
+                const int4 g0 = gc[k], g1 = gc[k + 1];
+                cnt += in_tube(g0, a, d, R) + in_tube(g1, a, d, R);
             }
+            if (k < end) cnt += in_tube(gc[k], a, d, R);
             if (cnt) atomicAdd(&scount[wib][own], cnt);
-        }
+        });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
@@ -302,30 +318,42 @@ __global__ void k_cand_keys(Batch b, Work w) {
     }
 }
 
-__global__ void __launch_bounds__(CT) k_member_fill(Batch b, Work w) {
+// Member lists of the candidates: the same warp-balanced walk as the counts;
+// each in-tube grain takes the next slot of its candidate's member range
+// (a shared-memory cursor), so the order inside a list is arbitrary.
+__global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     if (input_failed(b.ctl)) return;
     if (b.ctl->n_members > w.member_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&b.ctl->error, ERRB_OVF_MEMBERS);
         return;
     }
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
-    const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
-        const int lo = w.c_lo[c], hi = w.c_hi[c];
-        const int4 ga = b.gr[lo], gb = b.gr[hi];
-        const int3 a = make_int3(ga.x, ga.y, ga.z);
-        const int3 d = make_int3(gb.x - ga.x, gb.y - ga.y, gb.z - ga.z);
-        const long long R = b.r2 * ((long long)d.x * d.x + (long long)d.y * d.y + (long long)d.z * d.z);
-        const int v = view_of(b.goff, b.V, lo);
-        const u32 *cs = b.cell_start + (size_t)v * b.ncell;
-        u64 o = w.c_moff[c];
-        const u64 oend = w.c_moff[c + 1];
-        tube_cover(b, cs, a, d, [&](u32 beg, u32 end) {
-            for (u32 k = beg; k < end; ++k) {
-                const int4 g = b.gc[k];
-                if (in_tube(g, a, d, R) && o < oend) w.members[o++] = g.w;
+    __shared__ SeedSm sp[TW][32];
+    __shared__ unsigned long long cursor[TW][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const u64 nwarps = (u64)gridDim.x * TW;
+    const int4 *__restrict__ gc = b.gc;
+    int *__restrict__ members = w.members;
+    for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < nc; base += nwarps * 32) {
+        const u64 c = base + lane;
+        int n_items = 0;
+        if (c < nc) {
+            const int lo = w.c_lo[c], hi = w.c_hi[c];
+            SeedSm q;
+            n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
+            sp[wib][lane] = q;
+            cursor[wib][lane] = w.c_moff[c];
+        }
+        warp_items(b, sp[wib], n_items, [&](int own, const SeedSm &qq, u32 k, u32 end) {
+            const int3 a = make_int3(qq.ax, qq.ay, qq.az);
+            const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
+            const long long R = qq.R;
+            for (; k < end; ++k) {
+                const int4 g = gc[k];
+                if (in_tube(g, a, d, R)) members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
             }
         });
+        __syncwarp();
     }
 }
 
@@ -359,7 +387,7 @@ void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st) {
 }
 
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st) {
-    k_member_fill<<<persistent_grid(8), CT, 0, st>>>(b, w);
+    k_member_fill<<<persistent_grid(8), TW * 32, 0, st>>>(b, w);
 }
 
 }  // namespace et

@@ -77,17 +77,24 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     Ctl *ctl = b.ctl;
     if (input_failed(ctl)) return;   // decided before launch: uniform over the grid
     const u64 nc = min(ctl->n_cand, w.cand_cap);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const u32 H = (u32)b.H;
+    __shared__ int keep[MT / 32][32];   // per warp: undecided candidates waiting to be appended
     for (u32 round = 0;; ++round) {
         u64 *B = w.best[round & 1];
         u64 *Bp = w.best[(round + 1) & 1];
+        // candidates of this round: all of them first, then the carried list
+        const int *list = round == 0 ? nullptr : w.clist[round & 1];
+        const long long nl = round == 0 ? (long long)nc : (long long)__ldcg(&ctl->ncl[round & 1]);
+        if (blockIdx.x == 0 && threadIdx.x == 0) ctl->ncl[(round + 1) & 1] = 0;
         // ---- phase 1: reject hopeless candidates, post keys on unused grains
         u32 my_active = 0;
-        for (long long c = gwarp; c < (long long)nc; c += nwarps) {
-            if (w.c_state[c] != CS_UNDECIDED) continue;
+        for (long long i = gwarp; i < nl; i += nwarps) {
+            // lists and states are rewritten by other SMs between rounds: read through L2
+            const long long c = list ? __ldcg(&list[i]) : i;
+            if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             u32 nfree = 0;
             for (u64 base = m0; base < m1; base += 32) {
@@ -115,14 +122,19 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
         if (lane == 0 && my_active) atomicAdd(&ctl->active[round & 1], my_active);
         if (!grid_barrier(ctl, gridDim.x)) return;
         const u32 active = ld_cg_u32(&ctl->active[round & 1]);
+        if (blockIdx.x == 0 && threadIdx.x == 0 && round < 64) ctl->round_active[round] = active;
         if (active == 0) {
             if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
             return;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->active[(round + 1) & 1] = 0;
-        // ---- phase 2: accept ready candidates
-        for (long long c = gwarp; c < (long long)nc; c += nwarps) {
-            if (w.c_state[c] != CS_UNDECIDED) continue;
+        // ---- phase 2: accept ready candidates, carry the others to the next round
+        int *next = w.clist[(round + 1) & 1];
+        u64 *next_n = &ctl->ncl[(round + 1) & 1];
+        int nkeep = 0;   // warp-uniform
+        for (long long i = gwarp; i < nl; i += nwarps) {
+            const long long c = list ? __ldcg(&list[i]) : i;
+            if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             const u64 key = w.c_key[c];
             bool ready = true;
@@ -141,7 +153,19 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
                 }
                 nfree += __popc(__ballot_sync(0xffffffffu, fr));
             }
-            if (!ready) continue;
+            if (!ready) {
+                if (lane == 0) keep[wib][nkeep] = (int)c;
+                if (++nkeep == 32) {
+                    __syncwarp();
+                    u64 pos = 0;
+                    if (lane == 0) pos = atomicAdd(next_n, 32ull);
+                    pos = __shfl_sync(0xffffffffu, pos, 0);
+                    next[pos + lane] = keep[wib][lane];
+                    nkeep = 0;
+                    __syncwarp();
+                }
+                continue;
+            }
             // ready: the unused grains are exactly those where this key is the
             // minimum; nobody else can take them any more
             const bool accept = nfree >= H;
@@ -159,6 +183,14 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
                 w.c_nfree[c] = nfree;
                 w.c_state[c] = accept ? CS_ACCEPTED : CS_REJECTED;
             }
+        }
+        if (nkeep > 0) {
+            __syncwarp();
+            u64 pos = 0;
+            if (lane == 0) pos = atomicAdd(next_n, (u64)nkeep);
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (lane < nkeep) next[pos + lane] = keep[wib][lane];
+            __syncwarp();
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
     }

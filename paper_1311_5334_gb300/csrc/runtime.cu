@@ -150,6 +150,74 @@ void BatchRT::choose_cells() {
     ncell = (long long)nc[0] * nc[1] * nc[2];
 }
 
+// Autotuner: time the whole path for candidate cell shapes around the
+// density-based default s0 (about 0.35 grains per cell) and keep the fastest.
+et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, float *best_ms) {
+    if (!loaded) return fail(ET_ERR_NOT_READY, "no grains loaded");
+    if (!st) st = ctx->stream;
+    const double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
+    const double nmean = V > 0 ? std::max(1.0, (double)N / V) : 1.0;
+    const double s0 = std::cbrt(0.35 * vol / nmean);
+    // (x, y, z) factors of s0; rows run along x, so x cells may be short
+    static const double cand[][3] = {{1.0, 1.0, 1.0}, {1.3, 1.3, 1.3}, {0.33, 1.3, 1.3}, {0.33, 1.6, 1.6},
+                                     {0.8, 0.8, 0.8}, {0.5, 1.6, 1.3}, {0.33, 2.0, 2.0}, {1.6, 1.6, 1.6}};
+    const int ncand = (int)(sizeof cand / sizeof cand[0]);
+    if (max_trials <= 0 || max_trials > ncand) max_trials = ncand;
+    const et_tuning saved = tune;
+    const bool saved_prof = profile;
+    profile = true;
+    float best = 3.0e38f;
+    et_tuning best_t = tune;
+    for (int k = 0; k < max_trials; ++k) {
+        et_tuning t = saved;
+        for (int a = 0; a < 3; ++a)
+            t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k][a])));
+        tune = t;
+        choose_cells();
+        if ((double)V * (double)ncell >= 4.0e9) continue;
+        et_status s = reserve();
+        if (s != ET_OK) {
+            tune = saved;
+            profile = saved_prof;
+            return s;
+        }
+        float t_best = 3.0e38f;
+        for (int rep = 0; rep < 2; ++rep) {
+            s = enqueue(st, false);
+            if (s != ET_OK) {
+                tune = saved;
+                profile = saved_prof;
+                return s;
+            }
+            cudaEventRecord(done, st);
+            run_stream = st;
+            ran = true;
+            profiled_run = true;
+            s = settle(false);
+            if (s != ET_OK) {
+                tune = saved;
+                profile = saved_prof;
+                return s;
+            }
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev[0], ev[NSTAGE]) == cudaSuccess) t_best = std::min(t_best, ms);
+        }
+        if (t_best < best) {
+            best = t_best;
+            best_t = t;
+        }
+    }
+    profile = saved_prof;
+    tune = best_t;
+    choose_cells();
+    et_status s = reserve();
+    if (s != ET_OK) return s;
+    if (chosen) *chosen = best_t;
+    if (best_ms) *best_ms = best;
+    ran = false;
+    return ET_OK;
+}
+
 void BatchRT::estimate_caps() {
     const double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
     const double shell = 4.0 / 3.0 * M_PI *
@@ -226,6 +294,8 @@ et_status BatchRT::reserve() {
             c_moff = c.take<u64>(cc + 1);
             c_state = c.take<unsigned char>(cc);
             c_nfree = c.take<u32>(cc);
+            clist[0] = c.take<int>(cc);
+            clist[1] = c.take<int>(cc);
         };
         Carver cv;
         lay(cv);
@@ -379,6 +449,8 @@ Work BatchRT::dev_work() const {
     w.best[0] = best[0];
     w.best[1] = best[1];
     w.owner = owner;
+    w.clist[0] = clist[0];
+    w.clist[1] = clist[1];
     w.rec_lo = rec_lo;
     w.rec_hi = rec_hi;
     w.rec_cnt = rec_cnt;
@@ -785,6 +857,14 @@ et_status et_batch_set_tuning(et_batch *b, const et_tuning *t) {
     b->tune = *t;
     b->loaded = false;   // the cell grid changes: reload required
     return ET_OK;
+}
+
+et_status et_batch_autotune(et_batch *b, void *stream, int32_t max_trials, et_tuning *chosen, float *best_ms) {
+    GUARD_BEGIN
+    if (!b) return fail(ET_ERR_INVALID_ARG, "batch is NULL");
+    cudaSetDevice(b->ctx->device);
+    return b->autotune((cudaStream_t)stream, max_trials, chosen, best_ms);
+    GUARD_END
 }
 
 et_status et_batch_find(et_batch *b, void *stream, int32_t use_graph) {

@@ -59,6 +59,7 @@ struct BatchRT {
     u64 *seed_off = nullptr;
     u64 *best[2] = {nullptr, nullptr};
     int *owner = nullptr;
+    int *clist[2] = {nullptr, nullptr};
     u32 *cell_count = nullptr, *cell_start = nullptr;
     int2 *seeds = nullptr;
     int *c_lo = nullptr, *c_hi = nullptr;
@@ -90,6 +91,7 @@ struct BatchRT {
     BatchRT(Ctx *c, const et_params &pp);
     ~BatchRT();
     void choose_cells();
+    et_status autotune(cudaStream_t st, int max_trials, et_tuning *chosen, float *best_ms);
     void estimate_caps();
     et_status reserve();
     unsigned long long layout_generation() const;

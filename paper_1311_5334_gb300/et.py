@@ -97,6 +97,8 @@ _SIGS = {
     "et_batch_load": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "et_batch_set_tuning": (C.c_int32, [C.c_void_p, C.POINTER(Tuning)]),
     "et_batch_find": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "et_batch_autotune": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.POINTER(Tuning),
+                                      C.POINTER(C.c_float)]),
     "et_batch_fetch": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                                    C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "et_batch_stats": (C.c_int32, [C.c_void_p, C.POINTER(Stats)]),
@@ -278,6 +280,14 @@ class Batch:
 
     def find(self, stream=None, use_graph=False):
         _check(lib().et_batch_find(self._h, _stream_ptr(stream), 1 if use_graph else 0))
+
+    def autotune(self, stream=None, max_trials=0):
+        """Times the path for candidate cell shapes; keeps and returns the fastest
+        as (cell, ms per run)."""
+        t = Tuning()
+        ms = C.c_float()
+        _check(lib().et_batch_autotune(self._h, _stream_ptr(stream), int(max_trials), C.byref(t), C.byref(ms)))
+        return tuple(t.cell), float(ms.value)
 
     def sync(self):
         _check(lib().et_batch_sync(self._h))

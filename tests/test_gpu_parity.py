@@ -150,6 +150,25 @@ def test_cell_size_invariance(et, ctx, oracle_mod, cell):
     assert_same(et, tracks, members, want)
 
 
+def test_autotuner_keeps_results(et, ctx, oracle_mod):
+    views = [v for v in synth.batched(n_views=12, seed=6) if v.n < 20000][:6]
+    xyz, offs = synth.concat(views)
+    p = synth.params(views[0].extent)
+    b = et.Batch(ctx, p)
+    try:
+        b.load(xyz, offs)
+        cell, ms = b.autotune(max_trials=4)
+        assert all(c >= 16 for c in cell) and ms > 0
+        b.find(use_graph=True)
+        tracks, members, voff = b.fetch()
+        assert tuple(b.stats()["cell"]) == tuple(cell)
+        for k, v in enumerate(views):
+            want = oracle_run(oracle_mod, v.xyz, p)
+            assert et.track_tuples(tracks[voff[k]:voff[k + 1]], members) == want.as_tuples()
+    finally:
+        b.close()
+
+
 def test_permutation_invariance(et, ctx):
     v = synth.pr1()
     p = synth.params(v.extent)
