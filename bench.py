@@ -50,6 +50,21 @@ def dist_env():
     return ws, rank, local
 
 
+def reduce_max(value, dist=None, device=None):
+    """The timed region of the slowest rank (max over ranks); identity on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, n_ranks, max_ms):
+    """Units processed by all ranks per second of the slowest rank's timed region."""
+    return n_ranks * units_per_rank / (max_ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -259,14 +274,10 @@ def run_ours(args):
     barrier()
     wall = time.perf_counter() - t_wall0
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(float(np.sum(step_ms)), dist, device="cuda")
     ms_per_step = total_ms / args.steps
-    value = ws * n_views / (ms_per_step / 1e3)
-    seeds_per_s = ws * ref_stats["n_seeds"] / (ms_per_step / 1e3)
+    value = whole_job_rate(n_views, ws, ms_per_step)
+    seeds_per_s = whole_job_rate(ref_stats["n_seeds"], ws, ms_per_step)
 
     # roofline of the dominant kernel (tube counts): integer ALU issue
     tube_avg_ms = float(np.mean(tube_ms))
