@@ -237,11 +237,12 @@ def run_ours(args):
     batch.set_profiling(True)
     tuned = None
     if args.cell:
-        batch.set_tuning(tuple(int(c) for c in args.cell.split(",")))
+        batch.set_tuning(tuple(int(c) for c in args.cell.split(",")), row_lists=args.rows)
     batch.load(xyz_d, offs, stream=stream)
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
-        tuned = {"cell": list(cell), "ms_per_run": ms, "how": "et_batch_autotune: fastest of 8 cell shapes"}
+        tuned = {"cell": list(cell), "row_lists": batch.tuning["row_lists"], "ms_per_run": ms,
+                 "how": "et_batch_autotune: fastest of 8 cell shapes with x rows, then the best 2 with x+y rows"}
 
     def step():
         batch.load(xyz_d, offs, stream=stream)
@@ -433,6 +434,7 @@ def main():
                     help="time only the device-resident step (no plain/e2e/cpu baseline); for profilers")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched")
     ap.add_argument("--cell", default="", help="cell edges x,y,z in coordinate units (default: automatic)")
+    ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
     ap.add_argument("--served-rate", type=float, default=1000.0, help="Poisson rate of the served run (views/s)")
     ap.add_argument("--served-views", type=int, default=3000, help="views in the served run")
     ap.add_argument("--served-sweep", action="store_true",

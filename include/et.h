@@ -86,7 +86,9 @@ typedef struct {
 typedef struct {
     int32_t cell[3];        /* cell-list edge per axis, coordinate units */
     int32_t block_seeds;    /* reserved */
-    int32_t reserved[4];
+    int32_t row_lists;      /* 1: one cell list, rows along x; 2: also a list with rows
+                               along y, used by lines whose |w_y| > |w_x|; 0: automatic (1) */
+    int32_t reserved[3];
 } et_tuning;
 
 /* One reconstructed track.  seed_i / seed_j are indices into the caller's grain
@@ -204,9 +206,10 @@ et_status et_batch_load(et_batch *b, const int32_t *xyz, const int64_t *offsets,
 et_status et_batch_set_tuning(et_batch *b, const et_tuning *tuning);
 /* Picks the cell-list shape for the loaded batch by timing the whole path on
  * it: up to max_trials candidate shapes derived from the batch's mean grain
- * density (cubic and anisotropic, rows along x kept short), two runs each,
- * CUDA-event timed; the fastest is kept as the batch's tuning and returned in
- * *chosen (may be NULL), its time per run in *best_ms (may be NULL).
+ * density (cubic and anisotropic, rows along x kept short) with one cell list,
+ * then the two best shapes with both lists, two runs each, CUDA-event timed;
+ * the fastest is kept as the batch's tuning and returned in *chosen (may be
+ * NULL), its time per run in *best_ms (may be NULL).
  * Synchronous.  Results never depend on the choice, only the speed does. */
 et_status et_batch_autotune(et_batch *b, void *stream, int32_t max_trials, et_tuning *chosen, float *best_ms);
 /* Enqueues the path for all loaded views.  use_graph != 0 captures the launch

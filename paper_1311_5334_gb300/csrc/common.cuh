@@ -67,6 +67,14 @@ struct Batch {
     int4 *gr;            // canonical order: x, y, z, caller index within the view
     int4 *gc;            // cell order: x, y, z, canonical (global) index
     u32 *cell_start;     // V * ncell + 1
+    // second cell list with rows along y: cell edges (cs[1], cs[0], cs[2]),
+    // index cy + ncy[1] * (cx + ncy[0] * cz); lines whose |w_y| > |w_x| walk it
+    int dual;            // 1 if the second list is built and used
+    int csy[3], ncy[3];
+    float icsy[3];
+    int ncelly;
+    int4 *gcy;
+    u32 *cell_start_y;   // V * ncelly + 1
     Ctl *ctl;
 };
 
@@ -146,6 +154,8 @@ void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st
 void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u64 *ckeys, u32 *cvals,
                             u32 *cell_count, cudaStream_t st);
 void launch_cell_order(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
+void launch_y_keys(const Batch &b, u64 *keys, u32 *vals, u32 *cell_count, cudaStream_t st);
+void launch_cell_order_y(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
 
 // count.cu
 void launch_seed_count(const Batch &b, const Work &w, cudaStream_t st);

@@ -92,24 +92,24 @@ constexpr int TW = 8;   // warps per block
 struct SeedSm {
     int ax, ay, az, wx, wy, wz;      // grain a and w = b - a (exact test)
     long long R;                     // r^2 |w|^2
-    float xl0, xh0, fwx;             // x run: ax - pad, ax + pad, wx
+    float rl0, rh0, fwr, icsr;       // run axis (x, or y in the second list): a - pad, a + pad, w, 1/cell
+    int nr;                          // run-axis cell count
     float ao, wo, iwo, cso;          // outer axis: origin, direction, 1/w (0 if w = 0), cell edge
     float ai, wi, iwi, csi, ici;     // inner axis, ici = 1 / cell edge
     int nci, mo, mi;                 // inner cell count; row = co * mo + ci * mi
     float t0, t1;                    // parameter span of the line near the view
     int o0, excl;                    // first outer cell; first item index in the warp
-    u32 cs_off;                      // view offset in cell_start
+    u32 cs_off;                      // view offset in the cell list's start table
+    int ylist;                       // 1: the second cell list (rows along y)
 };
 
 // Resolves the cover geometry of the line through ga and gb into q and
 // returns its number of items (outer slabs).
 __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int view, SeedSm &q) {
     const float pad = (float)b.r + COVER_PAD;
-    const int ny = b.nc[1], nz = b.nc[2], nx = b.nc[0];
     q.ax = ga.x; q.ay = ga.y; q.az = ga.z;
     q.wx = gb.x - ga.x; q.wy = gb.y - ga.y; q.wz = gb.z - ga.z;
     q.R = b.r2 * ((long long)q.wx * q.wx + (long long)q.wy * q.wy + (long long)q.wz * q.wz);
-    q.cs_off = (u32)view * (u32)b.ncell;
     const float ax = (float)q.ax, ay = (float)q.ay, az = (float)q.az;
     const float wx = (float)q.wx, wy = (float)q.wy, wz = (float)q.wz;
     const float iwx = q.wx ? 1.0f / wx : 0.0f;
@@ -130,40 +130,66 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
     }
     q.t0 = t0;
     q.t1 = t1;
-    q.xl0 = ax - pad;
-    q.xh0 = ax + pad;
-    q.fwx = wx;
+    const float xl = ax + fminf(t0 * wx, t1 * wx) - pad, xh = ax + fmaxf(t0 * wx, t1 * wx) + pad;
     const float yl = ay + fminf(t0 * wy, t1 * wy) - pad, yh = ay + fmaxf(t0 * wy, t1 * wy) + pad;
     const float zl = az + fminf(t0 * wz, t1 * wz) - pad, zh = az + fmaxf(t0 * wz, t1 * wz) + pad;
-    const int cy0 = max(0, floor_i(yl * b.ics[1])), cy1 = min(ny - 1, floor_i(yh * b.ics[1]));
-    const int cz0 = max(0, floor_i(zl * b.ics[2])), cz1 = min(nz - 1, floor_i(zh * b.ics[2]));
-    const int nyc = max(0, cy1 - cy0 + 1), nzc = max(0, cz1 - cz0 + 1);
-    const float csy = (float)b.cs[1], csz = (float)b.cs[2];
-    if (nyc >= nzc) {   // outer y, inner z; row = (cz * ny + cy) * nx
-        q.ao = ay; q.wo = wy; q.iwo = iwy; q.cso = csy;
-        q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.ics[2]; q.nci = nz;
-        q.mo = nx; q.mi = ny * nx;
-        q.o0 = cy0;
-        return nyc;
+    // rows follow the line's dominant horizontal axis: x rows (first list) or y rows (second)
+    q.ylist = (b.dual && abs(q.wy) > abs(q.wx)) ? 1 : 0;
+    if (!q.ylist) {
+        const int nx = b.nc[0], ny = b.nc[1], nz = b.nc[2];
+        q.cs_off = (u32)view * (u32)b.ncell;
+        q.rl0 = ax - pad; q.rh0 = ax + pad; q.fwr = wx; q.icsr = b.ics[0]; q.nr = nx;
+        const int cy0 = max(0, floor_i(yl * b.ics[1])), cy1 = min(ny - 1, floor_i(yh * b.ics[1]));
+        const int cz0 = max(0, floor_i(zl * b.ics[2])), cz1 = min(nz - 1, floor_i(zh * b.ics[2]));
+        const int nyc = max(0, cy1 - cy0 + 1), nzc = max(0, cz1 - cz0 + 1);
+        const float csy = (float)b.cs[1], csz = (float)b.cs[2];
+        if (nyc >= nzc) {   // outer y, inner z; row = (cz * ny + cy) * nx
+            q.ao = ay; q.wo = wy; q.iwo = iwy; q.cso = csy;
+            q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.ics[2]; q.nci = nz;
+            q.mo = nx; q.mi = ny * nx;
+            q.o0 = cy0;
+            return nyc;
+        }
+        // outer z, inner y
+        q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
+        q.ai = ay; q.wi = wy; q.iwi = iwy; q.csi = csy; q.ici = b.ics[1]; q.nci = ny;
+        q.mo = ny * nx; q.mi = nx;
+        q.o0 = cz0;
+        return nzc;
     }
-    // outer z, inner y
+    // second list: rows along y, index cy + ny * (cx + nx * cz)
+    const int nx = b.ncy[0], ny = b.ncy[1], nz = b.ncy[2];
+    q.cs_off = (u32)view * (u32)b.ncelly;
+    q.rl0 = ay - pad; q.rh0 = ay + pad; q.fwr = wy; q.icsr = b.icsy[1]; q.nr = ny;
+    const int cx0 = max(0, floor_i(xl * b.icsy[0])), cx1 = min(nx - 1, floor_i(xh * b.icsy[0]));
+    const int cz0 = max(0, floor_i(zl * b.icsy[2])), cz1 = min(nz - 1, floor_i(zh * b.icsy[2]));
+    const int nxc = max(0, cx1 - cx0 + 1), nzc = max(0, cz1 - cz0 + 1);
+    const float csx = (float)b.csy[0], csz = (float)b.csy[2];
+    if (nxc >= nzc) {   // outer x, inner z; row = (cz * nx + cx) * ny
+        q.ao = ax; q.wo = wx; q.iwo = iwx; q.cso = csx;
+        q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.icsy[2]; q.nci = nz;
+        q.mo = ny; q.mi = nx * ny;
+        q.o0 = cx0;
+        return nxc;
+    }
+    // outer z, inner x
     q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
-    q.ai = ay; q.wi = wy; q.iwi = iwy; q.csi = csy; q.ici = b.ics[1]; q.nci = ny;
-    q.mo = ny * nx; q.mi = nx;
+    q.ai = ax; q.wi = wx; q.iwi = iwx; q.csi = csx; q.ici = b.icsy[0]; q.nci = nx;
+    q.mo = nx * ny; q.mi = ny;
     q.o0 = cz0;
     return nzc;
 }
 
-// Deals the items of the 32 lines in sp to the lanes of the warp and calls
-// f(owner_lane, qq, beg, end) for every row range of every item.  n_items is
+// Deals the items of the 32 lines in sp to the lanes of the warp.  For every
+// row range of an item it calls row(owner_lane, grains, a, d, R, beg, end),
+// which returns a count (grains: the cell-ordered array of the line's list);
+// after the item it calls done(owner_lane, sum of the counts).  n_items is
 // this lane's own line's item count (0 for an idle lane).
-template <class F>
-__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, F &&f) {
+template <class Row, class Done>
+__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, Row &&row_fn, Done &&done) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
     const float pad = (float)b.r + COVER_PAD;
-    const int nx = b.nc[0];
-    const float icsx = b.ics[0];
     int incl = n_items;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -201,9 +227,16 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
         const int ci0 = max(0, floor_i(il * qq.ici)), ci1 = min(qq.nci - 1, floor_i(ih * qq.ici));
         // inner slab ci spans t in [vb + ci*vs, vb + ci*vs + vw] (ordered by the sign of w)
         const float vs = csi * iwi, vb = (-pad - ai) * iwi, vw = (csi - 1.0f + 2.0f * pad) * iwi;
-        const float xl0 = qq.xl0, xh0 = qq.xh0, fwx = qq.fwx;
+        const float rl0 = qq.rl0, rh0 = qq.rh0, fwr = qq.fwr, icsr = qq.icsr;
+        const int nr = qq.nr;
         const int rowo = co * qq.mo, mi = qq.mi;
-        const u32 *__restrict__ cs = b.cell_start + qq.cs_off;
+        const bool ylist = qq.ylist != 0;
+        const u32 *__restrict__ cs = (ylist ? b.cell_start_y : b.cell_start) + qq.cs_off;
+        const int4 *__restrict__ gl = ylist ? b.gcy : b.gc;
+        const int3 a = make_int3(qq.ax, qq.ay, qq.az);
+        const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
+        const long long R = qq.R;
+        u32 sum = 0;
         for (int ci = ci0; ci <= ci1; ++ci) {
             float za = ta, zb = tb;
             if (wi != 0.0f) {
@@ -212,13 +245,14 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
                 zb = fminf(zb, fmaxf(v0, v1));
                 if (za > zb) continue;
             }
-            const float pa = za * fwx, pb = zb * fwx;
-            const int cx0 = max(0, floor_i((xl0 + fminf(pa, pb)) * icsx));
-            const int cx1 = min(nx - 1, floor_i((xh0 + fmaxf(pa, pb)) * icsx));
-            if (cx0 > cx1) continue;
+            const float pa = za * fwr, pb = zb * fwr;
+            const int cr0 = max(0, floor_i((rl0 + fminf(pa, pb)) * icsr));
+            const int cr1 = min(nr - 1, floor_i((rh0 + fmaxf(pa, pb)) * icsr));
+            if (cr0 > cr1) continue;
             const int row = rowo + ci * mi;
-            f(own, qq, cs[row + cx0], cs[row + cx1 + 1]);
+            sum += row_fn(own, gl, a, d, R, cs[row + cr0], cs[row + cr1 + 1]);
         }
+        done(own, sum);
     }
 }
 
@@ -233,7 +267,6 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     __shared__ u32 scount[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const u64 nwarps = (u64)gridDim.x * TW;
-    const int4 *__restrict__ gc = b.gc;
     u64 tests = 0, hits = 0;
     for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < ns; base += nwarps * 32) {
         const u64 s = base + lane;
@@ -241,7 +274,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         int lo = 0, hi = 0, n_items = 0;
         int cw = 0, cv = 0;
         if (valid) {
-            const int2 sd = w.seeds[s];
+            const int2 sd = __ldcs(&w.seeds[s]);   // read once: do not keep in L2
             lo = sd.x;
             hi = sd.y;
             const int4 ga = b.gr[lo], gb = b.gr[hi];
@@ -252,19 +285,21 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
             sp[wib][lane] = q;
         }
         scount[wib][lane] = 0;
-        warp_items(b, sp[wib], n_items, [&](int own, const SeedSm &qq, u32 k, u32 end) {
-            const int3 a = make_int3(qq.ax, qq.ay, qq.az);
-            const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
-            const long long R = qq.R;
-            tests += end - k;
-            u32 cnt = 0;
-            for (; k + 1 < end; k += 2) {
-                const int4 g0 = gc[k], g1 = gc[k + 1];
-                cnt += in_tube(g0, a, d, R) + in_tube(g1, a, d, R);
-            }
-            if (k < end) cnt += in_tube(gc[k], a, d, R);
-            if (cnt) atomicAdd(&scount[wib][own], cnt);
-        });
+        warp_items(
+            b, sp[wib], n_items,
+            [&](int, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 k, u32 end) -> u32 {
+                tests += end - k;
+                u32 cnt = 0;
+                for (; k + 1 < end; k += 2) {
+                    const int4 g0 = gc[k], g1 = gc[k + 1];
+                    cnt += in_tube(g0, a, d, R) + in_tube(g1, a, d, R);
+                }
+                if (k < end) cnt += in_tube(gc[k], a, d, R);
+                return cnt;
+            },
+            [&](int own, u32 cnt) {
+                if (cnt) atomicAdd(&scount[wib][own], cnt);
+            });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
@@ -332,27 +367,27 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     __shared__ unsigned long long cursor[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const u64 nwarps = (u64)gridDim.x * TW;
-    const int4 *__restrict__ gc = b.gc;
     int *__restrict__ members = w.members;
     for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < nc; base += nwarps * 32) {
         const u64 c = base + lane;
         int n_items = 0;
         if (c < nc) {
-            const int lo = w.c_lo[c], hi = w.c_hi[c];
+            const int lo = __ldcs(&w.c_lo[c]), hi = __ldcs(&w.c_hi[c]);
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
             sp[wib][lane] = q;
             cursor[wib][lane] = w.c_moff[c];
         }
-        warp_items(b, sp[wib], n_items, [&](int own, const SeedSm &qq, u32 k, u32 end) {
-            const int3 a = make_int3(qq.ax, qq.ay, qq.az);
-            const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
-            const long long R = qq.R;
-            for (; k < end; ++k) {
-                const int4 g = gc[k];
-                if (in_tube(g, a, d, R)) members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
-            }
-        });
+        warp_items(
+            b, sp[wib], n_items,
+            [&](int own, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 k, u32 end) -> u32 {
+                for (; k < end; ++k) {
+                    const int4 g = gc[k];
+                    if (in_tube(g, a, d, R)) members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
+                }
+                return 0u;
+            },
+            [&](int, u32) {});
         __syncwarp();
     }
 }

@@ -61,6 +61,31 @@ __global__ void k_cell_order(Batch b, const u32 *sorted_vals) {
     }
 }
 
+// Keys of the second cell list (rows along y) for the canonical order.
+__global__ void k_y_keys(Batch b, u64 *keys, u32 *vals, u32 *cell_count) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
+        const int v = view_of(b.goff, b.V, p);
+        const int4 g = b.gr[p];
+        const int cx = min(g.x / b.csy[0], b.ncy[0] - 1);
+        const int cy = min(g.y / b.csy[1], b.ncy[1] - 1);
+        const int cz = min(g.z / b.csy[2], b.ncy[2] - 1);
+        const u32 cell = (u32)v * (u32)b.ncelly + (u32)(cy + b.ncy[1] * (cx + b.ncy[0] * cz));
+        keys[p] = cell;
+        vals[p] = (u32)p;
+        atomicAdd(&cell_count[cell], 1u);
+    }
+}
+
+__global__ void k_cell_order_y(Batch b, const u32 *sorted_vals) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < b.N; q += stride) {
+        const u32 p = sorted_vals[q];
+        const int4 g = b.gr[p];
+        b.gcy[q] = make_int4(g.x, g.y, g.z, (int)p);
+    }
+}
+
 unsigned grid_for(long long n, int threads) {
     long long g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -81,6 +106,14 @@ void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u6
 
 void launch_cell_order(const Batch &b, const u32 *sorted_vals, cudaStream_t st) {
     k_cell_order<<<grid_for(b.N, 256), 256, 0, st>>>(b, sorted_vals);
+}
+
+void launch_y_keys(const Batch &b, u64 *keys, u32 *vals, u32 *cell_count, cudaStream_t st) {
+    k_y_keys<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals, cell_count);
+}
+
+void launch_cell_order_y(const Batch &b, const u32 *sorted_vals, cudaStream_t st) {
+    k_cell_order_y<<<grid_for(b.N, 256), 256, 0, st>>>(b, sorted_vals);
 }
 
 }  // namespace et

@@ -148,6 +148,14 @@ void BatchRT::choose_cells() {
         nc[k] = (p.extent[k] + cs[k] - 1) / cs[k];
     }
     ncell = (long long)nc[0] * nc[1] * nc[2];
+    // the second list swaps the x and y cell edges, so its rows (along y) are
+    // as short as the first list's rows (along x)
+    dual = tune.row_lists == 2;
+    csy[0] = std::max(1, std::min(cs[1], p.extent[0]));
+    csy[1] = std::max(1, std::min(cs[0], p.extent[1]));
+    csy[2] = cs[2];
+    for (int k = 0; k < 3; ++k) ncy[k] = (p.extent[k] + csy[k] - 1) / csy[k];
+    ncelly = dual ? (long long)ncy[0] * ncy[1] * ncy[2] : 1;
 }
 
 // Autotuner: time the whole path for candidate cell shapes around the
@@ -168,13 +176,26 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
     profile = true;
     float best = 3.0e38f;
     et_tuning best_t = tune;
-    for (int k = 0; k < max_trials; ++k) {
+    std::vector<std::pair<float, et_tuning>> tried;
+    for (int k = 0; k < max_trials + 2; ++k) {
         et_tuning t = saved;
-        for (int a = 0; a < 3; ++a)
-            t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k][a])));
+        if (k < max_trials) {
+            for (int a = 0; a < 3; ++a)
+                t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k][a])));
+            t.row_lists = 1;
+        } else {   // the two fastest shapes again, with the second (y-row) list
+            std::sort(tried.begin(), tried.end(),
+                      [](const std::pair<float, et_tuning> &x, const std::pair<float, et_tuning> &y) {
+                          return x.first < y.first;
+                      });
+            const size_t i = (size_t)(k - max_trials);
+            if (i >= tried.size()) break;
+            t = tried[i].second;
+            t.row_lists = 2;
+        }
         tune = t;
         choose_cells();
-        if ((double)V * (double)ncell >= 4.0e9) continue;
+        if ((double)V * (double)std::max(ncell, ncelly) >= 4.0e9) continue;
         et_status s = reserve();
         if (s != ET_OK) {
             tune = saved;
@@ -202,6 +223,7 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
             float ms = 0;
             if (cudaEventElapsedTime(&ms, ev[0], ev[NSTAGE]) == cudaSuccess) t_best = std::min(t_best, ms);
         }
+        if (k < max_trials) tried.push_back({t_best, t});
         if (t_best < best) {
             best = t_best;
             best_t = t;
@@ -258,6 +280,7 @@ et_status BatchRT::reserve() {
             vals[1] = c.take<u32>(n);
             gr = c.take<int4>(n);
             gc = c.take<int4>(n);
+            gcy = c.take<int4>(n);
             seed_off = c.take<u64>(n + 1);
             best[0] = c.take<u64>(n);
             best[1] = c.take<u64>(n);
@@ -268,15 +291,19 @@ et_status BatchRT::reserve() {
         Carver c2{0, g_grain.base};
         lay(c2);
     }
-    const size_t cells = (size_t)V * (size_t)ncell;
+    const size_t cells = (size_t)V * (size_t)ncell, cellsy = (size_t)V * (size_t)ncelly;
     {
+        auto lay = [&](Carver &c) {
+            cell_count = c.take<u32>(cells);
+            cell_start = c.take<u32>(cells + 1);
+            cell_count_y = c.take<u32>(cellsy);
+            cell_start_y = c.take<u32>(cellsy + 1);
+        };
         Carver cv;
-        cv.take<u32>(cells);
-        cv.take<u32>(cells + 1);
-        if (!g_cells.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "cell table (%zu bytes)", cv.off);
+        lay(cv);
+        if (!g_cells.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "cell tables (%zu bytes)", cv.off);
         Carver c2{0, g_cells.base};
-        cell_count = c2.take<u32>(cells);
-        cell_start = c2.take<u32>(cells + 1);
+        lay(c2);
     }
     {
         size_t need = want_seeds * sizeof(int2);
@@ -345,7 +372,7 @@ et_status BatchRT::reserve() {
         size_t t = 0;
         t = std::max(t, radix_temp_bytes((long long)n));
         t = std::max(t, radix_temp_bytes((long long)std::max<size_t>(cap_cand, n)));
-        t = std::max(t, scan_temp_bytes((long long)cells + 1));
+        t = std::max(t, scan_temp_bytes((long long)std::max(cells, cellsy) + 1));
         t = std::max(t, scan_temp_bytes((long long)n + 1));
         t = std::max(t, scan_temp_bytes((long long)cap_cand + 1));
         t = std::max(t, scan_temp_bytes((long long)V + 1));
@@ -386,7 +413,8 @@ et_status BatchRT::load(const int32_t *xyz, const int64_t *offsets, int nv, bool
     goff_h.assign(offsets, offsets + nv + 1);
     for (int k = 0; k < 3; ++k) cbits[k] = cb[k];
     choose_cells();
-    if ((double)V * (double)ncell >= 4.0e9) return fail(ET_ERR_INVALID_ARG, "cell table too large");
+    if ((double)V * (double)std::max(ncell, ncelly) >= 4.0e9)
+        return fail(ET_ERR_INVALID_ARG, "cell table too large");
     estimate_caps();
     et_status s = reserve();
     if (s != ET_OK) return s;
@@ -421,6 +449,15 @@ Batch BatchRT::dev_batch() const {
     b.smax2 = (long long)p.seed_max * p.seed_max;
     b.r2 = (long long)p.tube_r * p.tube_r;
     b.ncell = (int)ncell;
+    for (int k = 0; k < 3; ++k) {
+        b.csy[k] = csy[k];
+        b.ncy[k] = ncy[k];
+        b.icsy[k] = 1.0f / (float)csy[k];
+    }
+    b.ncelly = (int)ncelly;
+    b.dual = dual ? 1 : 0;
+    b.gcy = gcy;
+    b.cell_start_y = cell_start_y;
     b.vshift = cbits[0] + cbits[1] + cbits[2];
     b.xyz_in = xyz_in;
     b.gr = gr;
@@ -495,6 +532,15 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         int c2 = radix_sort_pairs(ok, ov, sk, sv, n, bits_for((unsigned long long)(cells - 1)), temp, st);
         launch_cell_order(b, c2 ? sv : ov, st);
         exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st);
+        if (dual) {   // second cell list (rows along y) from the same canonical order
+            const size_t cellsy = (size_t)V * (size_t)ncelly;
+            cudaMemsetAsync(cell_count_y, 0, sizeof(u32) * cellsy, st);
+            launch_y_keys(b, keys[0], vals[0], cell_count_y, st);
+            int c3 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n,
+                                      bits_for((unsigned long long)(cellsy - 1)), temp, st);
+            launch_cell_order_y(b, vals[c3], st);
+            exclusive_scan_u32(cell_count_y, cell_start_y, (long long)cellsy, temp, st);
+        }
         mark(1, st);
         launch_seed_count(b, w, st);
         exclusive_scan_u64(seed_off, seed_off, n, temp, &ctl->n_seeds, st);

@@ -44,6 +44,9 @@ struct BatchRT {
     std::vector<long long> goff_h;
     int cs[3] = {1, 1, 1}, nc[3] = {1, 1, 1}, cbits[3] = {0, 0, 0};
     long long ncell = 1;
+    int csy[3] = {1, 1, 1}, ncy[3] = {1, 1, 1};   // second cell list (rows along y)
+    long long ncelly = 1;
+    bool dual = false;
     // requested capacities
     u64 want_seeds = 0, want_cand = 0, want_members = 0, want_rec = 0;
     // granted capacities
@@ -61,6 +64,8 @@ struct BatchRT {
     int *owner = nullptr;
     int *clist[2] = {nullptr, nullptr};
     u32 *cell_count = nullptr, *cell_start = nullptr;
+    u32 *cell_count_y = nullptr, *cell_start_y = nullptr;
+    int4 *gcy = nullptr;
     int2 *seeds = nullptr;
     int *c_lo = nullptr, *c_hi = nullptr;
     u32 *c_cnt = nullptr, *c_nfree = nullptr;

@@ -38,7 +38,8 @@ class Params(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("cell", C.c_int32 * 3), ("block_seeds", C.c_int32), ("reserved", C.c_int32 * 4)]
+    _fields_ = [("cell", C.c_int32 * 3), ("block_seeds", C.c_int32), ("row_lists", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Stats(C.Structure):
@@ -258,10 +259,11 @@ class Batch:
         self._keep = None
         self.n_views = 0
 
-    def set_tuning(self, cell=(0, 0, 0)):
+    def set_tuning(self, cell=(0, 0, 0), row_lists=0):
         t = Tuning()
         for k in range(3):
             t.cell[k] = int(cell[k])
+        t.row_lists = int(row_lists)
         _check(lib().et_batch_set_tuning(self._h, C.byref(t)))
 
     def load(self, xyz, offsets, stream=None):
@@ -287,6 +289,7 @@ class Batch:
         t = Tuning()
         ms = C.c_float()
         _check(lib().et_batch_autotune(self._h, _stream_ptr(stream), int(max_trials), C.byref(t), C.byref(ms)))
+        self.tuning = {"cell": tuple(t.cell), "row_lists": int(t.row_lists)}
         return tuple(t.cell), float(ms.value)
 
     def sync(self):

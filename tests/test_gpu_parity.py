@@ -34,11 +34,11 @@ def ctx(et):
     c.close()
 
 
-def run_view(et, ctx, xyz, params, cell=None, seeds=False):
+def run_view(et, ctx, xyz, params, cell=None, seeds=False, row_lists=0):
     v = et.View.create(ctx, xyz, params)
     try:
-        if cell is not None:
-            v.set_tuning(cell)
+        if cell is not None or row_lists:
+            v.set_tuning(cell if cell is not None else (0, 0, 0), row_lists=row_lists)
             v.load_host(xyz)
         v.find()
         tracks, members = v.fetch()
@@ -116,8 +116,9 @@ def test_small_views_vs_brute_force(et, ctx, seed):
                         (30, 250, 8, 6), (10, 120, 15, 4)][seed]
     bs, bt = brute.find(xyz, smin, smax, r, h)
     p = dict(extent=extent, seed_min=smin, seed_max=smax, tube_r=r, min_hits=h)
-    for cell in [None, (97, 131, 53), (400, 400, 400), (17, 1200, 9), (1, 1, 1)]:
-        tracks, members, st, (si, sj, sc) = run_view(et, ctx, xyz, p, cell=cell, seeds=True)
+    for cell, rows in [(None, 0), ((97, 131, 53), 1), ((400, 400, 400), 1), ((17, 1200, 9), 1), ((1, 1, 1), 1),
+                       ((97, 131, 53), 2), ((17, 1200, 9), 2), ((300, 11, 50), 2)]:
+        tracks, members, st, (si, sj, sc) = run_view(et, ctx, xyz, p, cell=cell, seeds=True, row_lists=rows)
         assert {(int(a), int(b)): int(c) for a, b, c in zip(si, sj, sc)} == bs
         assert et.track_tuples(tracks, members) == bt
 
@@ -138,13 +139,14 @@ def test_workload_parity(et, ctx, oracle_mod, workload):
     check_fit(tracks, want)
 
 
-@pytest.mark.parametrize("cell", [(150, 150, 150), (300, 300, 100), (600, 600, 600), (1000, 250, 125),
-                                  (2000, 2000, 2000)])
-def test_cell_size_invariance(et, ctx, oracle_mod, cell):
+@pytest.mark.parametrize("cell,rows", [((150, 150, 150), 1), ((300, 300, 100), 1), ((600, 600, 600), 1),
+                                       ((1000, 250, 125), 1), ((2000, 2000, 2000), 1), ((150, 600, 600), 2),
+                                       ((1000, 250, 125), 2)])
+def test_cell_size_invariance(et, ctx, oracle_mod, cell, rows):
     v = synth.dense()
     p = synth.params(v.extent)
     want = oracle_run(oracle_mod, v.xyz, p)
-    tracks, members, st, _ = run_view(et, ctx, v.xyz, p, cell=cell)
+    tracks, members, st, _ = run_view(et, ctx, v.xyz, p, cell=cell, row_lists=rows)
     assert tuple(st["cell"]) == cell
     assert st["n_seeds"] == want.n_seeds
     assert_same(et, tracks, members, want)
