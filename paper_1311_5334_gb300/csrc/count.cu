@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
 // shared-memory atomics.  The geometry is the conservative cover of
 // tube_cover() (tube.cuh), with the per-slab terms hoisted.
 constexpr int TW = 8;   // warps per block
+constexpr int SEED_CHUNK = TW * 32 * 8;   // seeds per block work ticket
 
 struct SeedSm {
     int ax, ay, az, wx, wy, wz;      // grain a and w = b - a (exact test)
@@ -265,12 +266,21 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     }
     __shared__ SeedSm sp[TW][32];
     __shared__ u32 scount[TW][32];
+    __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const u64 nwarps = (u64)gridDim.x * TW;
     u64 tests = 0, hits = 0;
-    for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < ns; base += nwarps * 32) {
+    // blocks take contiguous chunks of the seed list (seeds of one view and of
+    // nearby origins), so the warps of a block share the view's cells in L1
+    for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[0], (u64)SEED_CHUNK);
+    __syncthreads();
+    const u64 c0 = chunk;
+    if (c0 >= ns) break;
+    const u64 c1 = min(c0 + (u64)SEED_CHUNK, ns);
+    for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
         const u64 s = base + lane;
-        const bool valid = s < ns;
+        const bool valid = s < c1;
         int lo = 0, hi = 0, n_items = 0;
         int cw = 0, cv = 0;
         if (valid) {
@@ -328,6 +338,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         }
         __syncwarp();
     }
+    }
     tests = warp_sum_u64(tests);
     hits = warp_sum_u64(hits);
     if (lane == 0) {
@@ -365,13 +376,20 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     __shared__ SeedSm sp[TW][32];
     __shared__ unsigned long long cursor[TW][32];
+    __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const u64 nwarps = (u64)gridDim.x * TW;
     int *__restrict__ members = w.members;
-    for (u64 base = ((u64)blockIdx.x * TW + wib) * 32; base < nc; base += nwarps * 32) {
+    for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[1], (u64)SEED_CHUNK);
+    __syncthreads();
+    const u64 c0 = chunk;
+    if (c0 >= nc) break;
+    const u64 c1 = min(c0 + (u64)SEED_CHUNK, nc);
+    for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
         const u64 c = base + lane;
         int n_items = 0;
-        if (c < nc) {
+        if (c < c1) {
             const int lo = __ldcs(&w.c_lo[c]), hi = __ldcs(&w.c_hi[c]);
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
@@ -389,6 +407,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
             },
             [&](int, u32) {});
         __syncwarp();
+    }
     }
 }
 
