@@ -90,95 +90,111 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
 constexpr int TW = 8;   // warps per block
 constexpr int SEED_CHUNK = TW * 32 * 8;   // seeds per block work ticket
 
-struct SeedSm {
-    int ax, ay, az, wx, wy, wz;      // grain a and w = b - a (exact test)
-    long long R;                     // r^2 |w|^2
-    float rl0, rh0, fwr, icsr;       // run axis (x, or y in the second list): a - pad, a + pad, w, 1/cell
-    int nr;                          // run-axis cell count
-    float ao, wo, iwo, cso;          // outer axis: origin, direction, 1/w (0 if w = 0), cell edge
-    float ai, wi, iwi, csi, ici;     // inner axis, ici = 1 / cell edge
-    int nci, mo, mi;                 // inner cell count; row = co * mo + ci * mi
-    float t0, t1;                    // parameter span of the line near the view
-    int o0, excl;                    // first outer cell; first item index in the warp
-    u32 cs_off;                      // view offset in the cell list's start table
-    int ylist;                       // 1: the second cell list (rows along y)
+// Cover geometry of one line, resolved once per line into eight 16-byte
+// vectors (loaded with eight vector loads per work item).  Slab t-intervals
+// are kept as (lower end at cell 0, step per cell, width) with the direction's
+// sign already folded in, so the walk needs no min/max to order their ends.
+struct __align__(16) SeedSm {
+    int4 e0;      // ax, ay, az, wx
+    int4 e1;      // wy, wz, R low, R high           (R = r^2 |w|^2)
+    float4 e2;    // t0, t1 (span of the line near the view), o0, excl (int bits)
+    float4 e3;    // outer slab: lower base, step, width; inner cell count (int bits)
+    float4 e4;    // inner slab: lower base, step, width, 1 / inner cell edge
+    float4 e5;    // inner axis: a - pad, a + pad, w, flags (int bits: 1 second list, 2 w_inner < 0, 4 w_run < 0)
+    float4 e6;    // run axis: a - pad, a + pad, w, 1 / run cell edge
+    int4 e7;      // run cell count, row stride of outer cell, of inner cell, view offset in the start table
 };
+
+// Slab k of a cell grid with edge cs spans coordinates [k cs, (k+1) cs - 1];
+// padded by pad, the line a + t w meets it for t in
+//   [base + k step, base + k step + width]
+// (w != 0).  w = 0: every t (the caller restricts k to the cells the line's
+// constant coordinate can reach).
+__device__ __forceinline__ float3 slab_coeffs(float a, float w, float iw, float cs, float pad) {
+    if (w == 0.0f) return make_float3(-3.0e38f, 0.0f, 6.0e38f);
+    const float step = cs * iw;
+    if (w > 0.0f) return make_float3((-pad - a) * iw, step, (cs - 1.0f + 2.0f * pad) * iw);
+    return make_float3((cs - 1.0f + pad - a) * iw, step, -(cs - 1.0f + 2.0f * pad) * iw);
+}
 
 // Resolves the cover geometry of the line through ga and gb into q and
 // returns its number of items (outer slabs).
 __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int view, SeedSm &q) {
     const float pad = (float)b.r + COVER_PAD;
-    q.ax = ga.x; q.ay = ga.y; q.az = ga.z;
-    q.wx = gb.x - ga.x; q.wy = gb.y - ga.y; q.wz = gb.z - ga.z;
-    q.R = b.r2 * ((long long)q.wx * q.wx + (long long)q.wy * q.wy + (long long)q.wz * q.wz);
-    const float ax = (float)q.ax, ay = (float)q.ay, az = (float)q.az;
-    const float wx = (float)q.wx, wy = (float)q.wy, wz = (float)q.wz;
-    const float iwx = q.wx ? 1.0f / wx : 0.0f;
-    const float iwy = q.wy ? 1.0f / wy : 0.0f;
-    const float iwz = q.wz ? 1.0f / wz : 0.0f;
+    const int wxi = gb.x - ga.x, wyi = gb.y - ga.y, wzi = gb.z - ga.z;
+    const long long R = b.r2 * ((long long)wxi * wxi + (long long)wyi * wyi + (long long)wzi * wzi);
+    q.e0 = make_int4(ga.x, ga.y, ga.z, wxi);
+    q.e1 = make_int4(wyi, wzi, (int)(unsigned)(R & 0xffffffffll), (int)(R >> 32));
+    const float ax = (float)ga.x, ay = (float)ga.y, az = (float)ga.z;
+    const float wx = (float)wxi, wy = (float)wyi, wz = (float)wzi;
+    const float iwx = wxi ? 1.0f / wx : 0.0f;
+    const float iwy = wyi ? 1.0f / wy : 0.0f;
+    const float iwz = wzi ? 1.0f / wz : 0.0f;
     float t0 = -3.0e38f, t1 = 3.0e38f;
-    if (q.wx) {
+    if (wxi) {
         float ta = (-pad - ax) * iwx, tb = ((float)(b.ext[0] - 1) + pad - ax) * iwx;
         t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
     }
-    if (q.wy) {
+    if (wyi) {
         float ta = (-pad - ay) * iwy, tb = ((float)(b.ext[1] - 1) + pad - ay) * iwy;
         t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
     }
-    if (q.wz) {
+    if (wzi) {
         float ta = (-pad - az) * iwz, tb = ((float)(b.ext[2] - 1) + pad - az) * iwz;
         t0 = fmaxf(t0, fminf(ta, tb)); t1 = fminf(t1, fmaxf(ta, tb));
     }
-    q.t0 = t0;
-    q.t1 = t1;
     const float xl = ax + fminf(t0 * wx, t1 * wx) - pad, xh = ax + fmaxf(t0 * wx, t1 * wx) + pad;
     const float yl = ay + fminf(t0 * wy, t1 * wy) - pad, yh = ay + fmaxf(t0 * wy, t1 * wy) + pad;
     const float zl = az + fminf(t0 * wz, t1 * wz) - pad, zh = az + fmaxf(t0 * wz, t1 * wz) + pad;
     // rows follow the line's dominant horizontal axis: x rows (first list) or y rows (second)
-    q.ylist = (b.dual && abs(q.wy) > abs(q.wx)) ? 1 : 0;
-    if (!q.ylist) {
+    const bool ylist = b.dual && abs(wyi) > abs(wxi);
+    // per axis: a, w, 1/w, cell edge, 1/cell edge, cells
+    float ra, rw, oa, ow, oiw, ocs, ia, iw, iiw, ics_, iinv, rinv;
+    int nr, o0, nitems, nci, mo, mi;
+    u32 cs_off;
+    if (!ylist) {
         const int nx = b.nc[0], ny = b.nc[1], nz = b.nc[2];
-        q.cs_off = (u32)view * (u32)b.ncell;
-        q.rl0 = ax - pad; q.rh0 = ax + pad; q.fwr = wx; q.icsr = b.ics[0]; q.nr = nx;
+        cs_off = (u32)view * (u32)b.ncell;
+        ra = ax; rw = wx; rinv = b.ics[0]; nr = nx;
         const int cy0 = max(0, floor_i(yl * b.ics[1])), cy1 = min(ny - 1, floor_i(yh * b.ics[1]));
         const int cz0 = max(0, floor_i(zl * b.ics[2])), cz1 = min(nz - 1, floor_i(zh * b.ics[2]));
         const int nyc = max(0, cy1 - cy0 + 1), nzc = max(0, cz1 - cz0 + 1);
-        const float csy = (float)b.cs[1], csz = (float)b.cs[2];
         if (nyc >= nzc) {   // outer y, inner z; row = (cz * ny + cy) * nx
-            q.ao = ay; q.wo = wy; q.iwo = iwy; q.cso = csy;
-            q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.ics[2]; q.nci = nz;
-            q.mo = nx; q.mi = ny * nx;
-            q.o0 = cy0;
-            return nyc;
+            oa = ay; ow = wy; oiw = iwy; ocs = (float)b.cs[1];
+            ia = az; iw = wz; iiw = iwz; ics_ = (float)b.cs[2]; iinv = b.ics[2]; nci = nz;
+            mo = nx; mi = ny * nx; o0 = cy0; nitems = nyc;
+        } else {            // outer z, inner y
+            oa = az; ow = wz; oiw = iwz; ocs = (float)b.cs[2];
+            ia = ay; iw = wy; iiw = iwy; ics_ = (float)b.cs[1]; iinv = b.ics[1]; nci = ny;
+            mo = ny * nx; mi = nx; o0 = cz0; nitems = nzc;
         }
-        // outer z, inner y
-        q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
-        q.ai = ay; q.wi = wy; q.iwi = iwy; q.csi = csy; q.ici = b.ics[1]; q.nci = ny;
-        q.mo = ny * nx; q.mi = nx;
-        q.o0 = cz0;
-        return nzc;
+    } else {                // second list: rows along y, index cy + ny * (cx + nx * cz)
+        const int nx = b.ncy[0], ny = b.ncy[1], nz = b.ncy[2];
+        cs_off = (u32)view * (u32)b.ncelly;
+        ra = ay; rw = wy; rinv = b.icsy[1]; nr = ny;
+        const int cx0 = max(0, floor_i(xl * b.icsy[0])), cx1 = min(nx - 1, floor_i(xh * b.icsy[0]));
+        const int cz0 = max(0, floor_i(zl * b.icsy[2])), cz1 = min(nz - 1, floor_i(zh * b.icsy[2]));
+        const int nxc = max(0, cx1 - cx0 + 1), nzc = max(0, cz1 - cz0 + 1);
+        if (nxc >= nzc) {   // outer x, inner z; row = (cz * nx + cx) * ny
+            oa = ax; ow = wx; oiw = iwx; ocs = (float)b.csy[0];
+            ia = az; iw = wz; iiw = iwz; ics_ = (float)b.csy[2]; iinv = b.icsy[2]; nci = nz;
+            mo = ny; mi = nx * ny; o0 = cx0; nitems = nxc;
+        } else {            // outer z, inner x
+            oa = az; ow = wz; oiw = iwz; ocs = (float)b.csy[2];
+            ia = ax; iw = wx; iiw = iwx; ics_ = (float)b.csy[0]; iinv = b.icsy[0]; nci = nx;
+            mo = nx * ny; mi = ny; o0 = cz0; nitems = nzc;
+        }
     }
-    // second list: rows along y, index cy + ny * (cx + nx * cz)
-    const int nx = b.ncy[0], ny = b.ncy[1], nz = b.ncy[2];
-    q.cs_off = (u32)view * (u32)b.ncelly;
-    q.rl0 = ay - pad; q.rh0 = ay + pad; q.fwr = wy; q.icsr = b.icsy[1]; q.nr = ny;
-    const int cx0 = max(0, floor_i(xl * b.icsy[0])), cx1 = min(nx - 1, floor_i(xh * b.icsy[0]));
-    const int cz0 = max(0, floor_i(zl * b.icsy[2])), cz1 = min(nz - 1, floor_i(zh * b.icsy[2]));
-    const int nxc = max(0, cx1 - cx0 + 1), nzc = max(0, cz1 - cz0 + 1);
-    const float csx = (float)b.csy[0], csz = (float)b.csy[2];
-    if (nxc >= nzc) {   // outer x, inner z; row = (cz * nx + cx) * ny
-        q.ao = ax; q.wo = wx; q.iwo = iwx; q.cso = csx;
-        q.ai = az; q.wi = wz; q.iwi = iwz; q.csi = csz; q.ici = b.icsy[2]; q.nci = nz;
-        q.mo = ny; q.mi = nx * ny;
-        q.o0 = cx0;
-        return nxc;
-    }
-    // outer z, inner x
-    q.ao = az; q.wo = wz; q.iwo = iwz; q.cso = csz;
-    q.ai = ax; q.wi = wx; q.iwi = iwx; q.csi = csx; q.ici = b.icsy[0]; q.nci = nx;
-    q.mo = nx * ny; q.mi = ny;
-    q.o0 = cz0;
-    return nzc;
+    const float3 os = slab_coeffs(oa, ow, oiw, ocs, pad);
+    const float3 is = slab_coeffs(ia, iw, iiw, ics_, pad);
+    const int flags = (ylist ? 1 : 0) | (iw < 0.0f ? 2 : 0) | (rw < 0.0f ? 4 : 0);
+    q.e2 = make_float4(t0, t1, __int_as_float(o0), __int_as_float(0));
+    q.e3 = make_float4(os.x, os.y, os.z, __int_as_float(nci));
+    q.e4 = make_float4(is.x, is.y, is.z, iinv);
+    q.e5 = make_float4(ia - pad, ia + pad, iw, __int_as_float(flags));
+    q.e6 = make_float4(ra - pad, ra + pad, rw, rinv);
+    q.e7 = make_int4(nr, mo, mi, (int)cs_off);
+    return nitems;
 }
 
 // Deals the items of the 32 lines in sp to the lanes of the warp.  For every
@@ -190,7 +206,6 @@ template <class Row, class Done>
 __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, Row &&row_fn, Done &&done) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
-    const float pad = (float)b.r + COVER_PAD;
     int incl = n_items;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -199,7 +214,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
     }
     const int excl = incl - n_items;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (n_items > 0) sp[lane].excl = excl;
+    if (n_items > 0) sp[lane].e2.w = __int_as_float(excl);
     __syncwarp();
     for (int ibase = 0; ibase < total; ibase += 32) {
         // lines whose first item falls in this round mark its position;
@@ -211,46 +226,35 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
         const int item = ibase + lane;
         if (item >= total) continue;
         const SeedSm &qq = sp[own];
-        const int co = qq.o0 + (item - qq.excl);
-        float ta = qq.t0, tb = qq.t1;
-        const float wo = qq.wo;
-        if (wo != 0.0f) {
-            const float cso = qq.cso, ao = qq.ao, iwo = qq.iwo;
-            const float u0 = ((float)co * cso - pad - ao) * iwo;
-            const float u1 = ((float)co * cso + cso - 1.0f + pad - ao) * iwo;
-            ta = fmaxf(ta, fminf(u0, u1));
-            tb = fminf(tb, fmaxf(u0, u1));
-        }
+        const float4 e2 = qq.e2, e3 = qq.e3;
+        const int co = __float_as_int(e2.z) + (item - __float_as_int(e2.w));
+        const float olo = fmaf((float)co, e3.y, e3.x);
+        const float ta = fmaxf(e2.x, olo), tb = fminf(e2.y, olo + e3.z);
         if (ta > tb) continue;
-        const float ai = qq.ai, wi = qq.wi, iwi = qq.iwi, csi = qq.csi;
-        const float il = ai + fminf(ta * wi, tb * wi) - pad;
-        const float ih = ai + fmaxf(ta * wi, tb * wi) + pad;
-        const int ci0 = max(0, floor_i(il * qq.ici)), ci1 = min(qq.nci - 1, floor_i(ih * qq.ici));
-        // inner slab ci spans t in [vb + ci*vs, vb + ci*vs + vw] (ordered by the sign of w)
-        const float vs = csi * iwi, vb = (-pad - ai) * iwi, vw = (csi - 1.0f + 2.0f * pad) * iwi;
-        const float rl0 = qq.rl0, rh0 = qq.rh0, fwr = qq.fwr, icsr = qq.icsr;
-        const int nr = qq.nr;
-        const int rowo = co * qq.mo, mi = qq.mi;
-        const bool ylist = qq.ylist != 0;
-        const u32 *__restrict__ cs = (ylist ? b.cell_start_y : b.cell_start) + qq.cs_off;
-        const int4 *__restrict__ gl = ylist ? b.gcy : b.gc;
-        const int3 a = make_int3(qq.ax, qq.ay, qq.az);
-        const int3 d = make_int3(qq.wx, qq.wy, qq.wz);
-        const long long R = qq.R;
+        const float4 e4 = qq.e4, e5 = qq.e5, e6 = qq.e6;
+        const int4 e7 = qq.e7;
+        const int flags = __float_as_int(e5.w);
+        const bool ineg = (flags & 2) != 0, rneg = (flags & 4) != 0;
+        // inner cells reached over [ta, tb]
+        const float il = fmaf(ineg ? tb : ta, e5.z, e5.x), ih = fmaf(ineg ? ta : tb, e5.z, e5.y);
+        const int nci = __float_as_int(e3.w);
+        const int ci0 = max(0, floor_i(il * e4.w)), ci1 = min(nci - 1, floor_i(ih * e4.w));
+        const u32 *__restrict__ cs = ((flags & 1) ? b.cell_start_y : b.cell_start) + (u32)e7.w;
+        const int4 *__restrict__ gl = (flags & 1) ? b.gcy : b.gc;
+        const int4 e0 = qq.e0, e1 = qq.e1;
+        const int3 a = make_int3(e0.x, e0.y, e0.z);
+        const int3 d = make_int3(e0.w, e1.x, e1.y);
+        const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
+        const int rowo = co * e7.y;
         u32 sum = 0;
         for (int ci = ci0; ci <= ci1; ++ci) {
-            float za = ta, zb = tb;
-            if (wi != 0.0f) {
-                const float v0 = vb + (float)ci * vs, v1 = v0 + vw;
-                za = fmaxf(za, fminf(v0, v1));
-                zb = fminf(zb, fmaxf(v0, v1));
-                if (za > zb) continue;
-            }
-            const float pa = za * fwr, pb = zb * fwr;
-            const int cr0 = max(0, floor_i((rl0 + fminf(pa, pb)) * icsr));
-            const int cr1 = min(nr - 1, floor_i((rh0 + fmaxf(pa, pb)) * icsr));
+            const float vlo = fmaf((float)ci, e4.y, e4.x);
+            const float za = fmaxf(ta, vlo), zb = fminf(tb, vlo + e4.z);
+            if (za > zb) continue;
+            const float r0 = fmaf(rneg ? zb : za, e6.z, e6.x), r1 = fmaf(rneg ? za : zb, e6.z, e6.y);
+            const int cr0 = max(0, floor_i(r0 * e6.w)), cr1 = min(e7.x - 1, floor_i(r1 * e6.w));
             if (cr0 > cr1) continue;
-            const int row = rowo + ci * mi;
+            const int row = rowo + ci * e7.z;
             sum += row_fn(own, gl, a, d, R, cs[row + cr0], cs[row + cr1 + 1]);
         }
         done(own, sum);
