@@ -88,7 +88,15 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
 // shared-memory atomics.  The geometry is the conservative cover of
 // tube_cover() (tube.cuh), with the per-slab terms hoisted.
 constexpr int TW = 8;   // warps per block
-constexpr int SEED_CHUNK = TW * 32 * 8;   // seeds per block work ticket
+constexpr int SEED_CHUNK = TW * 32 * 8;   // largest work ticket of a block (lines)
+
+// Ticket size: SEED_CHUNK lines, smaller when there are too few lines to give
+// every block of the grid a few tickets.
+__device__ __forceinline__ u64 ticket_size(u64 n) {
+    const u64 unit = TW * 32;
+    u64 c = (n / ((u64)gridDim.x * 4) + unit - 1) / unit * unit;
+    return c < unit ? unit : (c > (u64)SEED_CHUNK ? (u64)SEED_CHUNK : c);
+}
 
 // Cover geometry of one line, resolved once per line into eight 16-byte
 // vectors (loaded with eight vector loads per work item).  Slab t-intervals
@@ -275,13 +283,14 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     u64 tests = 0, hits = 0;
     // blocks take contiguous chunks of the seed list (seeds of one view and of
     // nearby origins), so the warps of a block share the view's cells in L1
+    const u64 tsize = ticket_size(ns);
     for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[0], (u64)SEED_CHUNK);
+    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[0], tsize);
     __syncthreads();
     const u64 c0 = chunk;
     if (c0 >= ns) break;
-    const u64 c1 = min(c0 + (u64)SEED_CHUNK, ns);
+    const u64 c1 = min(c0 + tsize, ns);
     for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
         const u64 s = base + lane;
         const bool valid = s < c1;
@@ -383,13 +392,14 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *__restrict__ members = w.members;
+    const u64 tsize = ticket_size(nc);
     for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[1], (u64)SEED_CHUNK);
+    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[1], tsize);
     __syncthreads();
     const u64 c0 = chunk;
     if (c0 >= nc) break;
-    const u64 c1 = min(c0 + (u64)SEED_CHUNK, nc);
+    const u64 c1 = min(c0 + tsize, nc);
     for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
         const u64 c = base + lane;
         int n_items = 0;
