@@ -41,6 +41,10 @@ METRIC = "views/s"
 # One tube-membership test: 3 IADD (offset), 6 IMUL/IMAD (int32 cross product),
 # 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
 OPS_PER_TEST = 14
+# DRAM bytes the tube-count kernel moves per seed (dram__bytes_read.sum +
+# dram__bytes_write.sum of one ncu capture on the dense view: 21.95 MB for
+# 2,571,392 seeds); a launch's traffic is scaled by its seed count.
+TUBE_DRAM_BYTES_PER_SEED = 21.954048e6 / 2571392
 
 
 def dist_env():
@@ -311,7 +315,8 @@ def run_ours(args):
             "stage_ms": stage_ms,
             "wall_s": wall,
             "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
-                         "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved / peak,
+                         "traffic": TUBE_DRAM_BYTES_PER_SEED * ref_stats["n_seeds"],
                          "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
                                   f"{tube_avg_ms:.3f} ms (in-graph CUDA events); peak = "
                                   f"{info['sm_count']} SMs x 128 lanes x 2070 MHz"},
