@@ -96,6 +96,21 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             const long long c = list ? __ldcg(&list[i]) : i;
             if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
+            if (m1 - m0 <= 32) {   // one chunk: member and its state stay in registers
+                const u64 m = m0 + lane;
+                const bool in = m < m1;
+                const int g = in ? w.members[m] : 0;
+                if (in && round > 0) Bp[g] = ~0ull;
+                const bool fr = in && __ldcg(&w.owner[g]) < 0;
+                const u32 nfree = __popc(__ballot_sync(0xffffffffu, fr));
+                if (nfree < H) {
+                    if (lane == 0) w.c_state[c] = CS_REJECTED;
+                    continue;
+                }
+                if (fr) atomicMin(&B[g], w.c_key[c]);
+                ++my_active;
+                continue;
+            }
             u32 nfree = 0;
             for (u64 base = m0; base < m1; base += 32) {
                 const u64 m = base + lane;
@@ -137,6 +152,37 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             const u64 key = w.c_key[c];
+            if (m1 - m0 <= 32) {   // one chunk: member and its state stay in registers
+                const u64 m = m0 + lane;
+                const bool in = m < m1;
+                const int g = in ? w.members[m] : 0;
+                const bool fr = in && __ldcg(&w.owner[g]) < 0;
+                const bool bad = fr && __ldcg(&B[g]) != key;
+                if (__any_sync(0xffffffffu, bad)) {
+                    if (lane == 0) keep[wib][nkeep] = (int)c;
+                    if (++nkeep == 32) {
+                        __syncwarp();
+                        u64 pos = 0;
+                        if (lane == 0) pos = atomicAdd(next_n, 32ull);
+                        pos = __shfl_sync(0xffffffffu, pos, 0);
+                        next[pos + lane] = keep[wib][lane];
+                        nkeep = 0;
+                        __syncwarp();
+                    }
+                    continue;
+                }
+                const u32 nfree = __popc(__ballot_sync(0xffffffffu, fr));
+                const bool accept = nfree >= H;
+                if (fr) {
+                    if (accept) w.owner[g] = (int)c;
+                    B[g] = ~0ull;
+                }
+                if (lane == 0) {
+                    w.c_nfree[c] = nfree;
+                    w.c_state[c] = accept ? CS_ACCEPTED : CS_REJECTED;
+                }
+                continue;
+            }
             bool ready = true;
             u32 nfree = 0;
             for (u64 base = m0; base < m1; base += 32) {
