@@ -205,11 +205,34 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
     return nitems;
 }
 
-// Deals the items of the 32 lines in sp to the lanes of the warp.  For every
-// row range of an item it calls row(owner_lane, grains, a, d, R, beg, end),
-// which returns a count (grains: the cell-ordered array of the line's list);
-// after the item it calls done(owner_lane, sum of the counts).  n_items is
-// this lane's own line's item count (0 for an idle lane).
+// Calls f(g) for the grains gl[b0 .. b0+n0) and then gl[b1 .. b1+n1), two
+// at a time: one loop over both rows, so lanes whose rows split differently
+// still run their tests together.
+template <class F>
+__device__ __forceinline__ void for_grains2(const int4 *__restrict__ gl, u32 b0, u32 n0, u32 b1, u32 n1, F &&f) {
+    const u32 e0 = b0 + n0;
+    u32 k = b0, left = n0 + n1;
+    for (; left >= 2; left -= 2) {
+        if (k == e0) k = b1;
+        u32 k1 = k + 1;
+        if (k1 == e0) k1 = b1;
+        const int4 g0 = gl[k], g1 = gl[k1];
+        f(g0);
+        f(g1);
+        k = k1 + 1;
+    }
+    if (left) {
+        if (k == e0) k = b1;
+        f(gl[k]);
+    }
+}
+
+// Deals the items of the 32 lines in sp to the lanes of the warp.  An item's
+// non-empty row ranges are gathered first; the first two go to one call
+// row(owner_lane, grains, a, d, R, b0, n0, b1, n1) (grains: the cell-ordered
+// array of the line's list), a rare third or later row to a call of its own.
+// row returns a count; after the item done(owner_lane, sum of the counts) is
+// called.  n_items is this lane's own line's item count (0 for an idle lane).
 template <class Row, class Done>
 __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, Row &&row_fn, Done &&done) {
     const int lane = threadIdx.x & 31;
@@ -255,6 +278,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
         const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
         const int rowo = co * e7.y;
         u32 sum = 0;
+        u32 b0 = 0, n0 = 0, b1 = 0, n1 = 0;
         for (int ci = ci0; ci <= ci1; ++ci) {
             const float vlo = fmaf((float)ci, e4.y, e4.x);
             const float za = fmaxf(ta, vlo), zb = fminf(tb, vlo + e4.z);
@@ -263,8 +287,19 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
             const int cr0 = max(0, floor_i(r0 * e6.w)), cr1 = min(e7.x - 1, floor_i(r1 * e6.w));
             if (cr0 > cr1) continue;
             const int row = rowo + ci * e7.z;
-            sum += row_fn(own, gl, a, d, R, cs[row + cr0], cs[row + cr1 + 1]);
+            const u32 beg = cs[row + cr0], end = cs[row + cr1 + 1];
+            if (end == beg) continue;
+            if (n0 == 0) {
+                b0 = beg;
+                n0 = end - beg;
+            } else if (n1 == 0) {
+                b1 = beg;
+                n1 = end - beg;
+            } else {
+                sum += row_fn(own, gl, a, d, R, beg, end - beg, 0u, 0u);
+            }
         }
+        sum += row_fn(own, gl, a, d, R, b0, n0, b1, n1);
         done(own, sum);
     }
 }
@@ -310,14 +345,11 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         scount[wib][lane] = 0;
         warp_items(
             b, sp[wib], n_items,
-            [&](int, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 k, u32 end) -> u32 {
-                tests += end - k;
+            [&](int, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 b0, u32 n0, u32 b1,
+                u32 n1) -> u32 {
+                tests += n0 + n1;
                 u32 cnt = 0;
-                for (; k + 1 < end; k += 2) {
-                    const int4 g0 = gc[k], g1 = gc[k + 1];
-                    cnt += in_tube(g0, a, d, R) + in_tube(g1, a, d, R);
-                }
-                if (k < end) cnt += in_tube(gc[k], a, d, R);
+                for_grains2(gc, b0, n0, b1, n1, [&](int4 g) { cnt += in_tube(g, a, d, R); });
                 return cnt;
             },
             [&](int own, u32 cnt) {
@@ -412,11 +444,11 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
         }
         warp_items(
             b, sp[wib], n_items,
-            [&](int own, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 k, u32 end) -> u32 {
-                for (; k < end; ++k) {
-                    const int4 g = gc[k];
+            [&](int own, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 b0, u32 n0, u32 b1,
+                u32 n1) -> u32 {
+                for_grains2(gc, b0, n0, b1, n1, [&](int4 g) {
                     if (in_tube(g, a, d, R)) members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
-                }
+                });
                 return 0u;
             },
             [&](int, u32) {});
