@@ -205,38 +205,26 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
     return nitems;
 }
 
-// Calls f(g) for the grains gl[b0 .. b0+n0) and then gl[b1 .. b1+n1), two
-// at a time: one loop over both rows, so lanes whose rows split differently
-// still run their tests together.
-template <class F>
-__device__ __forceinline__ void for_grains2(const int4 *__restrict__ gl, u32 b0, u32 n0, u32 b1, u32 n1, F &&f) {
-    const u32 e0 = b0 + n0;
-    u32 k = b0, left = n0 + n1;
-    for (; left >= 2; left -= 2) {
-        if (k == e0) k = b1;
-        u32 k1 = k + 1;
-        if (k1 == e0) k1 = b1;
-        const int4 g0 = gl[k], g1 = gl[k1];
-        f(g0);
-        f(g1);
-        k = k1 + 1;
-    }
-    if (left) {
-        if (k == e0) k = b1;
-        f(gl[k]);
-    }
-}
-
-// Deals the items of the 32 lines in sp to the lanes of the warp.  An item's
-// non-empty row ranges are gathered first; the first two go to one call
-// row(owner_lane, grains, a, d, R, b0, n0, b1, n1) (grains: the cell-ordered
-// array of the line's list), a rare third or later row to a call of its own.
-// row returns a count; after the item done(owner_lane, sum of the counts) is
-// called.  n_items is this lane's own line's item count (0 for an idle lane).
-template <class Row, class Done>
-__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_items, Row &&row_fn, Done &&done) {
+// Deals the items of the 32 lines in sp to the lanes of the warp and tests
+// the grains of their cell runs; hit(owner_line, g) is called for every grain
+// g inside the owner line's tube.  n_items is this lane's own line's item
+// count (0 for an idle lane); tests counts the membership tests this lane
+// performs.
+//
+// A round gives one item to each lane.  The lane resolves the item's non-empty
+// row ranges (usually one or two; a rare third or later row is tested by the
+// lane itself).  The warp then deals all grains of the round's first two row
+// ranges to its lanes, 32 at a time: lane j takes grain base + j of the
+// concatenated ranges, finds the range owning it from the ranges that start
+// in this pass (an OR-reduction of one-hot start bits and a popcount) and reads
+// the range from a per-warp table (tbl) indexed by that rank.  So every pass
+// tests 32 grains, however unevenly the rows of the round hold them.
+template <class Hit>
+__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl, int n_items, u64 &tests,
+                                           Hit &&hit) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
+    const unsigned lane_lt = lane_le >> 1;
     int incl = n_items;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -255,52 +243,99 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int n_ite
         const int before = __popc(__ballot_sync(0xffffffffu, n_items > 0 && excl < ibase));
         const int own = before + __popc(smask & lane_le) - 1;
         const int item = ibase + lane;
-        if (item >= total) continue;
-        const SeedSm &qq = sp[own];
-        const float4 e2 = qq.e2, e3 = qq.e3;
-        const int co = __float_as_int(e2.z) + (item - __float_as_int(e2.w));
-        const float olo = fmaf((float)co, e3.y, e3.x);
-        const float ta = fmaxf(e2.x, olo), tb = fminf(e2.y, olo + e3.z);
-        if (ta > tb) continue;
-        const float4 e4 = qq.e4, e5 = qq.e5, e6 = qq.e6;
-        const int4 e7 = qq.e7;
-        const int flags = __float_as_int(e5.w);
-        const bool ineg = (flags & 2) != 0, rneg = (flags & 4) != 0;
-        // inner cells reached over [ta, tb]
-        const float il = fmaf(ineg ? tb : ta, e5.z, e5.x), ih = fmaf(ineg ? ta : tb, e5.z, e5.y);
-        const int nci = __float_as_int(e3.w);
-        const int ci0 = max(0, floor_i(il * e4.w)), ci1 = min(nci - 1, floor_i(ih * e4.w));
-        const u32 *__restrict__ cs = ((flags & 1) ? b.cell_start_y : b.cell_start) + (u32)e7.w;
-        const int4 *__restrict__ gl = (flags & 1) ? b.gcy : b.gc;
-        const int4 e0 = qq.e0, e1 = qq.e1;
-        const int3 a = make_int3(e0.x, e0.y, e0.z);
-        const int3 d = make_int3(e0.w, e1.x, e1.y);
-        const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
-        const int rowo = co * e7.y;
-        u32 sum = 0;
         u32 b0 = 0, n0 = 0, b1 = 0, n1 = 0;
-        for (int ci = ci0; ci <= ci1; ++ci) {
-            const float vlo = fmaf((float)ci, e4.y, e4.x);
-            const float za = fmaxf(ta, vlo), zb = fminf(tb, vlo + e4.z);
-            if (za > zb) continue;
-            const float r0 = fmaf(rneg ? zb : za, e6.z, e6.x), r1 = fmaf(rneg ? za : zb, e6.z, e6.y);
-            const int cr0 = max(0, floor_i(r0 * e6.w)), cr1 = min(e7.x - 1, floor_i(r1 * e6.w));
-            if (cr0 > cr1) continue;
-            const int row = rowo + ci * e7.z;
-            const u32 beg = cs[row + cr0], end = cs[row + cr1 + 1];
-            if (end == beg) continue;
-            if (n0 == 0) {
-                b0 = beg;
-                n0 = end - beg;
-            } else if (n1 == 0) {
-                b1 = beg;
-                n1 = end - beg;
-            } else {
-                sum += row_fn(own, gl, a, d, R, beg, end - beg, 0u, 0u);
+        int list = 0;
+        if (item < total) {
+            const SeedSm &qq = sp[own];
+            const float4 e2 = qq.e2, e3 = qq.e3;
+            const int co = __float_as_int(e2.z) + (item - __float_as_int(e2.w));
+            const float olo = fmaf((float)co, e3.y, e3.x);
+            const float ta = fmaxf(e2.x, olo), tb = fminf(e2.y, olo + e3.z);
+            if (ta <= tb) {
+                const float4 e4 = qq.e4, e5 = qq.e5, e6 = qq.e6;
+                const int4 e7 = qq.e7;
+                const int flags = __float_as_int(e5.w);
+                list = flags & 1;
+                const bool ineg = (flags & 2) != 0, rneg = (flags & 4) != 0;
+                // inner cells reached over [ta, tb]
+                const float il = fmaf(ineg ? tb : ta, e5.z, e5.x), ih = fmaf(ineg ? ta : tb, e5.z, e5.y);
+                const int nci = __float_as_int(e3.w);
+                const int ci0 = max(0, floor_i(il * e4.w)), ci1 = min(nci - 1, floor_i(ih * e4.w));
+                const u32 *__restrict__ cs = (list ? b.cell_start_y : b.cell_start) + (u32)e7.w;
+                const int rowo = co * e7.y;
+                for (int ci = ci0; ci <= ci1; ++ci) {
+                    const float vlo = fmaf((float)ci, e4.y, e4.x);
+                    const float za = fmaxf(ta, vlo), zb = fminf(tb, vlo + e4.z);
+                    if (za > zb) continue;
+                    const float r0 = fmaf(rneg ? zb : za, e6.z, e6.x), r1 = fmaf(rneg ? za : zb, e6.z, e6.y);
+                    const int cr0 = max(0, floor_i(r0 * e6.w)), cr1 = min(e7.x - 1, floor_i(r1 * e6.w));
+                    if (cr0 > cr1) continue;
+                    const int row = rowo + ci * e7.z;
+                    const u32 beg = cs[row + cr0], end = cs[row + cr1 + 1];
+                    if (end == beg) continue;
+                    if (n0 == 0) {
+                        b0 = beg;
+                        n0 = end - beg;
+                    } else if (n1 == 0) {
+                        b1 = beg;
+                        n1 = end - beg;
+                    } else {   // rare: a third row, tested by this lane alone
+                        const int4 *__restrict__ gl = list ? b.gcy : b.gc;
+                        const int4 e0 = qq.e0, e1 = qq.e1;
+                        const int3 a = make_int3(e0.x, e0.y, e0.z), d = make_int3(e0.w, e1.x, e1.y);
+                        const long long R =
+                            (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
+                        tests += end - beg;
+                        for (u32 k = beg; k < end; ++k) {
+                            const int4 g = gl[k];
+                            if (in_tube(g, a, d, R)) hit(own, g);
+                        }
+                    }
+                }
             }
         }
-        sum += row_fn(own, gl, a, d, R, b0, n0, b1, n1);
-        done(own, sum);
+        // deal the grains of all lanes' first two rows over the warp
+        const u32 n = n0 + n1;
+        tests += n;
+        u32 rin = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 v = __shfl_up_sync(0xffffffffu, rin, o);
+            if (lane >= o) rin += v;
+        }
+        const u32 rtotal = __shfl_sync(0xffffffffu, rin, 31);
+        const u32 rex = rin - n;
+        const unsigned nonempty = __ballot_sync(0xffffffffu, n > 0);
+        if (n > 0)
+            tbl[__popc(nonempty & lane_lt)] =
+                make_int4((int)(b0 - rex), (int)(rex + n0), (int)(b1 - rex - n0), own | (list << 8));
+        __syncwarp();
+        // two passes per iteration, so that their table, geometry and grain
+        // loads overlap
+        for (u32 base = 0; base < rtotal; base += 64) {
+            const bool st0 = n > 0 && rex >= base && rex < base + 32;
+            const bool st1 = n > 0 && rex >= base + 32 && rex < base + 64;
+            const unsigned sm0 = __reduce_or_sync(0xffffffffu, st0 ? (1u << (rex - base)) : 0u);
+            const unsigned sm1 = __reduce_or_sync(0xffffffffu, st1 ? (1u << (rex - base - 32)) : 0u);
+            const unsigned bm = __ballot_sync(0xffffffffu, n > 0 && rex < base);
+            const int bef0 = __popc(bm), bef1 = bef0 + __popc(sm0);
+            const u32 i0 = base + lane, i1 = i0 + 32;
+            const bool v0 = i0 < rtotal, v1 = i1 < rtotal;
+            const int4 t0 = tbl[v0 ? bef0 + __popc(sm0 & lane_le) - 1 : 0];
+            const int4 t1 = tbl[v1 ? bef1 + __popc(sm1 & lane_le) - 1 : 0];
+            const u32 k0 = i0 + (u32)(i0 < (u32)t0.y ? t0.x : t0.z);
+            const u32 k1 = i1 + (u32)(i1 < (u32)t1.y ? t1.x : t1.z);
+            const int ow0 = t0.w & 0xff, ow1 = t1.w & 0xff;
+            const int4 p0 = sp[ow0].e0, q0 = sp[ow0].e1, p1 = sp[ow1].e0, q1 = sp[ow1].e1;
+            int4 g0 = make_int4(0, 0, 0, 0), g1 = make_int4(0, 0, 0, 0);
+            if (v0) g0 = ((t0.w >> 8) ? b.gcy : b.gc)[k0];
+            if (v1) g1 = ((t1.w >> 8) ? b.gcy : b.gc)[k1];
+            const long long R0 = (long long)(((unsigned long long)(unsigned)q0.w << 32) | (unsigned)q0.z);
+            const long long R1 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned)q1.z);
+            if (v0 && in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
+            if (v1 && in_tube(g1, make_int3(p1.x, p1.y, p1.z), make_int3(p1.w, q1.x, q1.y), R1)) hit(ow1, g1);
+        }
+        __syncwarp();   // the table is rewritten by the next round
     }
 }
 
@@ -312,6 +347,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         return;
     }
     __shared__ SeedSm sp[TW][32];
+    __shared__ int4 tbl[TW][32];
     __shared__ u32 scount[TW][32];
     __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -343,18 +379,9 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
             sp[wib][lane] = q;
         }
         scount[wib][lane] = 0;
-        warp_items(
-            b, sp[wib], n_items,
-            [&](int, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 b0, u32 n0, u32 b1,
-                u32 n1) -> u32 {
-                tests += n0 + n1;
-                u32 cnt = 0;
-                for_grains2(gc, b0, n0, b1, n1, [&](int4 g) { cnt += in_tube(g, a, d, R); });
-                return cnt;
-            },
-            [&](int own, u32 cnt) {
-                if (cnt) atomicAdd(&scount[wib][own], cnt);
-            });
+        __syncwarp();
+        warp_items(b, sp[wib], tbl[wib], n_items, tests,
+                   [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
@@ -420,6 +447,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     }
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     __shared__ SeedSm sp[TW][32];
+    __shared__ int4 tbl[TW][32];
     __shared__ unsigned long long cursor[TW][32];
     __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -442,16 +470,11 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
             sp[wib][lane] = q;
             cursor[wib][lane] = w.c_moff[c];
         }
-        warp_items(
-            b, sp[wib], n_items,
-            [&](int own, const int4 *__restrict__ gc, int3 a, int3 d, long long R, u32 b0, u32 n0, u32 b1,
-                u32 n1) -> u32 {
-                for_grains2(gc, b0, n0, b1, n1, [&](int4 g) {
-                    if (in_tube(g, a, d, R)) members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
-                });
-                return 0u;
-            },
-            [&](int, u32) {});
+        __syncwarp();
+        u64 tests = 0;
+        warp_items(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
+            members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
+        });
         __syncwarp();
     }
     }
