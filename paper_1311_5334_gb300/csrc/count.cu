@@ -263,15 +263,42 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
                 const int ci0 = max(0, floor_i(il * e4.w)), ci1 = min(nci - 1, floor_i(ih * e4.w));
                 const u32 *__restrict__ cs = (list ? b.cell_start_y : b.cell_start) + (u32)e7.w;
                 const int rowo = co * e7.y;
-                for (int ci = ci0; ci <= ci1; ++ci) {
+                // cell run of inner cell ci: [s0, s1) into cs, or s0 = s1 = 0
+                auto run = [&](int ci, int &s0, int &s1) {
+                    s0 = s1 = 0;
                     const float vlo = fmaf((float)ci, e4.y, e4.x);
                     const float za = fmaxf(ta, vlo), zb = fminf(tb, vlo + e4.z);
-                    if (za > zb) continue;
                     const float r0 = fmaf(rneg ? zb : za, e6.z, e6.x), r1 = fmaf(rneg ? za : zb, e6.z, e6.y);
                     const int cr0 = max(0, floor_i(r0 * e6.w)), cr1 = min(e7.x - 1, floor_i(r1 * e6.w));
-                    if (cr0 > cr1) continue;
-                    const int row = rowo + ci * e7.z;
-                    const u32 beg = cs[row + cr0], end = cs[row + cr1 + 1];
+                    if (za <= zb && cr0 <= cr1 && ci <= ci1) {
+                        const int row = rowo + ci * e7.z;
+                        s0 = row + cr0;
+                        s1 = row + cr1 + 1;
+                    }
+                };
+                // the first two inner cells (almost every item has at most two):
+                // their four start-table loads are issued together
+                int sa0, sa1, sb0, sb1;
+                run(ci0, sa0, sa1);
+                run(ci0 + 1, sb0, sb1);
+                const u32 ba = cs[sa0], ea = cs[sa1], bb = cs[sb0], eb = cs[sb1];
+                if (ea != ba) {
+                    b0 = ba;
+                    n0 = ea - ba;
+                }
+                if (eb != bb) {
+                    if (n0 == 0) {
+                        b0 = bb;
+                        n0 = eb - bb;
+                    } else {
+                        b1 = bb;
+                        n1 = eb - bb;
+                    }
+                }
+                for (int ci = ci0 + 2; ci <= ci1; ++ci) {
+                    int s0, s1;
+                    run(ci, s0, s1);
+                    const u32 beg = cs[s0], end = cs[s1];
                     if (end == beg) continue;
                     if (n0 == 0) {
                         b0 = beg;
@@ -311,8 +338,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
                 make_int4((int)(b0 - rex), (int)(rex + n0), (int)(b1 - rex - n0), own | (list << 8));
         __syncwarp();
         // two passes per iteration, so that their table, geometry and grain
-        // loads overlap
-        for (u32 base = 0; base < rtotal; base += 64) {
+        // loads overlap; a last part of at most 32 grains takes one pass
+        u32 base = 0;
+        for (; base + 32 < rtotal; base += 64) {
             const bool st0 = n > 0 && rex >= base && rex < base + 32;
             const bool st1 = n > 0 && rex >= base + 32 && rex < base + 64;
             const unsigned sm0 = __reduce_or_sync(0xffffffffu, st0 ? (1u << (rex - base)) : 0u);
@@ -320,20 +348,35 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
             const unsigned bm = __ballot_sync(0xffffffffu, n > 0 && rex < base);
             const int bef0 = __popc(bm), bef1 = bef0 + __popc(sm0);
             const u32 i0 = base + lane, i1 = i0 + 32;
-            const bool v0 = i0 < rtotal, v1 = i1 < rtotal;
-            const int4 t0 = tbl[v0 ? bef0 + __popc(sm0 & lane_le) - 1 : 0];
+            const bool v1 = i1 < rtotal;
+            const int4 t0 = tbl[bef0 + __popc(sm0 & lane_le) - 1];
             const int4 t1 = tbl[v1 ? bef1 + __popc(sm1 & lane_le) - 1 : 0];
             const u32 k0 = i0 + (u32)(i0 < (u32)t0.y ? t0.x : t0.z);
             const u32 k1 = i1 + (u32)(i1 < (u32)t1.y ? t1.x : t1.z);
             const int ow0 = t0.w & 0xff, ow1 = t1.w & 0xff;
             const int4 p0 = sp[ow0].e0, q0 = sp[ow0].e1, p1 = sp[ow1].e0, q1 = sp[ow1].e1;
-            int4 g0 = make_int4(0, 0, 0, 0), g1 = make_int4(0, 0, 0, 0);
-            if (v0) g0 = ((t0.w >> 8) ? b.gcy : b.gc)[k0];
+            const int4 g0 = ((t0.w >> 8) ? b.gcy : b.gc)[k0];
+            int4 g1 = make_int4(0, 0, 0, 0);
             if (v1) g1 = ((t1.w >> 8) ? b.gcy : b.gc)[k1];
             const long long R0 = (long long)(((unsigned long long)(unsigned)q0.w << 32) | (unsigned)q0.z);
             const long long R1 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned)q1.z);
-            if (v0 && in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
+            if (in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
             if (v1 && in_tube(g1, make_int3(p1.x, p1.y, p1.z), make_int3(p1.w, q1.x, q1.y), R1)) hit(ow1, g1);
+        }
+        if (base < rtotal) {
+            const bool st = n > 0 && rex >= base && rex < base + 32;
+            const unsigned sm = __reduce_or_sync(0xffffffffu, st ? (1u << (rex - base)) : 0u);
+            const int bef = __popc(__ballot_sync(0xffffffffu, n > 0 && rex < base));
+            const u32 i = base + lane;
+            if (i < rtotal) {
+                const int4 t = tbl[bef + __popc(sm & lane_le) - 1];
+                const u32 k = i + (u32)(i < (u32)t.y ? t.x : t.z);
+                const int ow = t.w & 0xff;
+                const int4 e0 = sp[ow].e0, e1 = sp[ow].e1;
+                const int4 g = ((t.w >> 8) ? b.gcy : b.gc)[k];
+                const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
+                if (in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R)) hit(ow, g);
+            }
         }
         __syncwarp();   // the table is rewritten by the next round
     }
