@@ -88,13 +88,13 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
 // shared-memory atomics.  The geometry is the conservative cover of
 // tube_cover() (tube.cuh), with the per-slab terms hoisted.
 constexpr int TW = 8;   // warps per block
-constexpr int SEED_CHUNK = TW * 32 * 8;   // largest work ticket of a block (lines)
+constexpr int SEED_CHUNK = 32 * 8;   // largest work ticket of a warp (lines)
 
 // Ticket size: SEED_CHUNK lines, smaller when there are too few lines to give
-// every block of the grid a few tickets.
+// every warp of the grid a few tickets.
 __device__ __forceinline__ u64 ticket_size(u64 n) {
-    const u64 unit = TW * 32;
-    u64 c = (n / ((u64)gridDim.x * 4) + unit - 1) / unit * unit;
+    const u64 unit = 32;
+    u64 c = (n / ((u64)gridDim.x * TW * 4) + unit - 1) / unit * unit;
     return c < unit ? unit : (c > (u64)SEED_CHUNK ? (u64)SEED_CHUNK : c);
 }
 
@@ -111,6 +111,32 @@ struct __align__(16) SeedSm {
     float4 e5;    // inner axis: a - pad, a + pad, w, flags (int bits: 1 second list, 2 w_inner < 0, 4 w_run < 0)
     float4 e6;    // run axis: a - pad, a + pad, w, 1 / run cell edge
     int4 e7;      // run cell count, row stride of outer cell, of inner cell, view offset in the start table
+};
+
+// The records of a warp's 32 lines, vector k of line i at v[k][i]: a lane
+// storing its own record writes consecutive 16-byte slots (no bank
+// conflicts), and lanes reading different lines' vector k mostly hit
+// different banks.
+struct SeedTab {
+    int4 v[8][32];
+    __device__ __forceinline__ void put(int i, const SeedSm &q) {
+        v[0][i] = q.e0;
+        v[1][i] = q.e1;
+        v[2][i] = f4i(q.e2);
+        v[3][i] = f4i(q.e3);
+        v[4][i] = f4i(q.e4);
+        v[5][i] = f4i(q.e5);
+        v[6][i] = f4i(q.e6);
+        v[7][i] = q.e7;
+    }
+    __device__ __forceinline__ int4 i4(int k, int i) const { return v[k][i]; }
+    __device__ __forceinline__ float4 f4(int k, int i) const {
+        const int4 t = v[k][i];
+        return make_float4(__int_as_float(t.x), __int_as_float(t.y), __int_as_float(t.z), __int_as_float(t.w));
+    }
+    static __device__ __forceinline__ int4 f4i(float4 f) {
+        return make_int4(__float_as_int(f.x), __float_as_int(f.y), __float_as_int(f.z), __float_as_int(f.w));
+    }
 };
 
 // Slab k of a cell grid with edge cs spans coordinates [k cs, (k+1) cs - 1];
@@ -220,7 +246,7 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
 // the range from a per-warp table (tbl) indexed by that rank.  So every pass
 // tests 32 grains, however unevenly the rows of the round hold them.
 template <class Hit>
-__device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl, int n_items, u64 &tests,
+__device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u64 &tests,
                                            Hit &&hit) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
@@ -233,7 +259,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
     }
     const int excl = incl - n_items;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (n_items > 0) sp[lane].e2.w = __int_as_float(excl);
+    if (n_items > 0) sp.v[2][lane].w = excl;
     __syncwarp();
     for (int ibase = 0; ibase < total; ibase += 32) {
         // lines whose first item falls in this round mark its position;
@@ -246,14 +272,13 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
         u32 b0 = 0, n0 = 0, b1 = 0, n1 = 0;
         int list = 0;
         if (item < total) {
-            const SeedSm &qq = sp[own];
-            const float4 e2 = qq.e2, e3 = qq.e3;
+            const float4 e2 = sp.f4(2, own), e3 = sp.f4(3, own);
             const int co = __float_as_int(e2.z) + (item - __float_as_int(e2.w));
             const float olo = fmaf((float)co, e3.y, e3.x);
             const float ta = fmaxf(e2.x, olo), tb = fminf(e2.y, olo + e3.z);
             if (ta <= tb) {
-                const float4 e4 = qq.e4, e5 = qq.e5, e6 = qq.e6;
-                const int4 e7 = qq.e7;
+                const float4 e4 = sp.f4(4, own), e5 = sp.f4(5, own), e6 = sp.f4(6, own);
+                const int4 e7 = sp.i4(7, own);
                 const int flags = __float_as_int(e5.w);
                 list = flags & 1;
                 const bool ineg = (flags & 2) != 0, rneg = (flags & 4) != 0;
@@ -308,7 +333,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
                         n1 = end - beg;
                     } else {   // rare: a third row, tested by this lane alone
                         const int4 *__restrict__ gl = list ? b.gcy : b.gc;
-                        const int4 e0 = qq.e0, e1 = qq.e1;
+                        const int4 e0 = sp.i4(0, own), e1 = sp.i4(1, own);
                         const int3 a = make_int3(e0.x, e0.y, e0.z), d = make_int3(e0.w, e1.x, e1.y);
                         const long long R =
                             (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
@@ -354,7 +379,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
             const u32 k0 = i0 + (u32)(i0 < (u32)t0.y ? t0.x : t0.z);
             const u32 k1 = i1 + (u32)(i1 < (u32)t1.y ? t1.x : t1.z);
             const int ow0 = t0.w & 0xff, ow1 = t1.w & 0xff;
-            const int4 p0 = sp[ow0].e0, q0 = sp[ow0].e1, p1 = sp[ow1].e0, q1 = sp[ow1].e1;
+            const int4 p0 = sp.i4(0, ow0), q0 = sp.i4(1, ow0), p1 = sp.i4(0, ow1), q1 = sp.i4(1, ow1);
             const int4 g0 = ((t0.w >> 8) ? b.gcy : b.gc)[k0];
             int4 g1 = make_int4(0, 0, 0, 0);
             if (v1) g1 = ((t1.w >> 8) ? b.gcy : b.gc)[k1];
@@ -372,7 +397,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedSm *sp, int4 *tbl
                 const int4 t = tbl[bef + __popc(sm & lane_le) - 1];
                 const u32 k = i + (u32)(i < (u32)t.y ? t.x : t.z);
                 const int ow = t.w & 0xff;
-                const int4 e0 = sp[ow].e0, e1 = sp[ow].e1;
+                const int4 e0 = sp.i4(0, ow), e1 = sp.i4(1, ow);
                 const int4 g = ((t.w >> 8) ? b.gcy : b.gc)[k];
                 const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
                 if (in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R)) hit(ow, g);
@@ -389,23 +414,21 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&b.ctl->error, ERRB_OVF_RECORD);
         return;
     }
-    __shared__ SeedSm sp[TW][32];
+    __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
     __shared__ u32 scount[TW][32];
-    __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     u64 tests = 0, hits = 0;
-    // blocks take contiguous chunks of the seed list (seeds of one view and of
-    // nearby origins), so the warps of a block share the view's cells in L1
+    // warps take contiguous chunks of the seed list (seeds of one view and of
+    // nearby origins) from a ticket counter; no block-wide barrier
     const u64 tsize = ticket_size(ns);
     for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[0], tsize);
-    __syncthreads();
-    const u64 c0 = chunk;
+    u64 c0 = 0;
+    if (lane == 0) c0 = atomicAdd(&b.ctl->ticket[0], tsize);
+    c0 = __shfl_sync(0xffffffffu, c0, 0);
     if (c0 >= ns) break;
     const u64 c1 = min(c0 + tsize, ns);
-    for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
+    for (u64 base = c0; base < c1; base += 32) {
         const u64 s = base + lane;
         const bool valid = s < c1;
         int lo = 0, hi = 0, n_items = 0;
@@ -419,7 +442,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
             cv = gb.w;
             SeedSm q;
             n_items = seed_setup(b, ga, gb, view_of(b.goff, b.V, lo), q);
-            sp[wib][lane] = q;
+            sp[wib].put(lane, q);
         }
         scount[wib][lane] = 0;
         __syncwarp();
@@ -489,28 +512,26 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
         return;
     }
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
-    __shared__ SeedSm sp[TW][32];
+    __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
     __shared__ unsigned long long cursor[TW][32];
-    __shared__ u64 chunk;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *__restrict__ members = w.members;
     const u64 tsize = ticket_size(nc);
     for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) chunk = atomicAdd(&b.ctl->ticket[1], tsize);
-    __syncthreads();
-    const u64 c0 = chunk;
+    u64 c0 = 0;
+    if (lane == 0) c0 = atomicAdd(&b.ctl->ticket[1], tsize);
+    c0 = __shfl_sync(0xffffffffu, c0, 0);
     if (c0 >= nc) break;
     const u64 c1 = min(c0 + tsize, nc);
-    for (u64 base = c0 + (u64)wib * 32; base < c1; base += TW * 32) {
+    for (u64 base = c0; base < c1; base += 32) {
         const u64 c = base + lane;
         int n_items = 0;
         if (c < c1) {
             const int lo = __ldcs(&w.c_lo[c]), hi = __ldcs(&w.c_hi[c]);
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
-            sp[wib][lane] = q;
+            sp[wib].put(lane, q);
             cursor[wib][lane] = w.c_moff[c];
         }
         __syncwarp();
