@@ -246,7 +246,7 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
 // the range from a per-warp table (tbl) indexed by that rank.  So every pass
 // tests 32 grains, however unevenly the rows of the round hold them.
 template <class Hit>
-__device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u64 &tests,
+__device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u32 &tests,
                                            Hit &&hit) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     __shared__ int4 tbl[TW][32];
     __shared__ u32 scount[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    u64 tests = 0, hits = 0;
+    u32 tests = 0, hits = 0;   // per thread: far below 2^32 in one launch
     // warps take contiguous chunks of the seed list (seeds of one view and of
     // nearby origins) from a ticket counter; no block-wide barrier
     const u64 tsize = ticket_size(ns);
@@ -427,21 +427,17 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
     if (lane == 0) c0 = atomicAdd(&b.ctl->ticket[0], tsize);
     c0 = __shfl_sync(0xffffffffu, c0, 0);
     if (c0 >= ns) break;
-    const u64 c1 = min(c0 + tsize, ns);
-    for (u64 base = c0; base < c1; base += 32) {
-        const u64 s = base + lane;
-        const bool valid = s < c1;
+    const u32 len = (u32)min(tsize, ns - c0);
+    for (u32 o = 0; o < len; o += 32) {
+        const bool valid = o + lane < len;
+        const u64 s = c0 + o + lane;
         int lo = 0, hi = 0, n_items = 0;
-        int cw = 0, cv = 0;
         if (valid) {
             const int2 sd = __ldcs(&w.seeds[s]);   // read once: do not keep in L2
             lo = sd.x;
             hi = sd.y;
-            const int4 ga = b.gr[lo], gb = b.gr[hi];
-            cw = ga.w;
-            cv = gb.w;
             SeedSm q;
-            n_items = seed_setup(b, ga, gb, view_of(b.goff, b.V, lo), q);
+            n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
             sp[wib].put(lane, q);
         }
         scount[wib][lane] = 0;
@@ -452,8 +448,8 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
         if (valid && record) {
-            w.rec_lo[s] = cw;
-            w.rec_hi[s] = cv;
+            w.rec_lo[s] = b.gr[lo].w;
+            w.rec_hi[s] = b.gr[hi].w;
             w.rec_cnt[s] = (int)count;
         }
         const bool is_cand = valid && count >= (u32)b.H;
@@ -477,11 +473,10 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         __syncwarp();
     }
     }
-    tests = warp_sum_u64(tests);
-    hits = warp_sum_u64(hits);
+    const u64 wtests = warp_sum_u64(tests), whits = warp_sum_u64(hits);
     if (lane == 0) {
-        if (tests) atomicAdd(&b.ctl->n_tests, tests);
-        if (hits) atomicAdd(&b.ctl->n_hits, hits);
+        if (wtests) atomicAdd(&b.ctl->n_tests, wtests);
+        if (whits) atomicAdd(&b.ctl->n_hits, whits);
     }
 }
 
@@ -535,7 +530,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
             cursor[wib][lane] = w.c_moff[c];
         }
         __syncwarp();
-        u64 tests = 0;
+        u32 tests = 0;
         warp_items(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
             members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
         });
