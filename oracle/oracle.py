@@ -1,4 +1,4 @@
-"""ctypes wrapper around the C oracle (oracle.c).
+"""ctypes wrapper around the C oracle (oracle.c, frames.c).
 
 TEST INFRASTRUCTURE ONLY: used by tests/, by __graft_entry__.smoke() and by
 the CPU-baseline leg of bench.py.  The product path (the CUDA library and its
@@ -7,7 +7,9 @@ binding) never imports this module.
 The oracle is the plain definition of Section 2 of the paper (seeds = grain
 pairs within a distance window, count of grains along each seed line,
 threshold, exclusive grain association) evaluated on the CPU with exact
-integer arithmetic, plus an FP64 orthogonal least-squares fit.
+integer arithmetic, plus an FP64 orthogonal least-squares fit; and the image
+front end of the same section (pixel filtering and 3D grain recognition,
+frames.c), also in exact integer arithmetic.
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "oracle.c")
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "frames.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
 
@@ -57,13 +59,14 @@ _lock = threading.Lock()
 
 
 def build(force=False, quiet=True):
-    """Compile oracle.c with gcc (-O2, OpenMP) into oracle/_build/liboracle.so."""
+    """Compile oracle.c and frames.c with gcc (-O2, OpenMP) into oracle/_build/liboracle.so."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    if (not force and os.path.exists(_LIB_PATH)
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-Wno-unused-parameter", _SRC, "-o", tmp, "-lm"]
+           "-Wno-unused-parameter", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True, capture_output=quiet)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -96,6 +99,12 @@ def lib():
             L.or_tracks_free.argtypes = [C.POINTER(_Tracks)]
             L.or_sym_eigen3.argtypes = [PD, PD, PD]
             L.or_fit.argtypes = [C.c_void_p, P32, C.c_int64, C.c_int32, C.c_int32, PD, PD, PD, PD]
+            PU8 = C.POINTER(C.c_uint8)
+            L.or_frames_filter.restype = C.c_int
+            L.or_frames_filter.argtypes = [PU8, C.c_int64, C.c_int32, C.c_int32, C.c_int32, PU8, PU8, PU8]
+            L.or_frames_grains.restype = C.c_int64
+            L.or_frames_grains.argtypes = [PU8, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P32, P32,
+                                           P32, P32, P64, C.c_int64]
             _lib = L
     return _lib
 
@@ -254,3 +263,50 @@ def sym_eigen3(m):
     lam, vec = np.zeros(3), np.zeros(9)
     lib().or_sym_eigen3(_pd(m), _pd(lam), _pd(vec))
     return lam, vec.reshape(3, 3)
+
+
+# ---------------------------------------------------------------- image front end
+
+
+def _pu8(a):
+    return a.ctypes.data_as(C.POINTER(C.c_uint8))
+
+
+def frames_filter(raw, gain, thr):
+    """Filtered pulse heights (uint8 [D][H][W]) of one view's raw frames.
+
+    raw: uint8 [D][H][P] with P >= W row pitch (only the first W columns are
+    pixels); gain, thr: uint8 [H][W] per-pixel gain (128 = 1.0) and threshold.
+    """
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    gain = np.ascontiguousarray(gain, dtype=np.uint8)
+    thr = np.ascontiguousarray(thr, dtype=np.uint8)
+    D, H, P = raw.shape
+    W = gain.shape[1]
+    if gain.shape != (H, W) or thr.shape != (H, W) or P < W:
+        raise OracleError(INVALID_ARG, "frames_filter shapes")
+    out = np.zeros((D, H, W), dtype=np.uint8)
+    st = lib().or_frames_filter(_pu8(raw), P, W, H, D, _pu8(gain), _pu8(thr), _pu8(out))
+    if st != OK:
+        raise OracleError(st, "or_frames_filter")
+    return out
+
+
+def frames_grains(filt, threshold, num, den):
+    """Grains of one filtered view (uint8 [D][H][W]) in raster order of their
+    defining voxel: (xyz int32 [n][3], pulse int32 [n], voxel int64 [n])."""
+    filt = np.ascontiguousarray(filt, dtype=np.uint8)
+    D, H, W = filt.shape
+    num = np.ascontiguousarray(num, dtype=np.int32)
+    den = np.ascontiguousarray(den, dtype=np.int32)
+    L = lib()
+    n = L.or_frames_grains(_pu8(filt), W, H, D, int(threshold), _p32(num), _p32(den), None, None, None, 0)
+    if n < 0:
+        raise OracleError(int(n), "or_frames_grains")
+    xyz = np.zeros((max(n, 1), 3), dtype=np.int32)
+    pulse = np.zeros(max(n, 1), dtype=np.int32)
+    voxel = np.zeros(max(n, 1), dtype=np.int64)
+    got = L.or_frames_grains(_pu8(filt), W, H, D, int(threshold), _p32(num), _p32(den), _p32(xyz),
+                             _p32(pulse), voxel.ctypes.data_as(C.POINTER(C.c_int64)), n)
+    assert got == n
+    return xyz[:n], pulse[:n], voxel[:n]

@@ -218,3 +218,99 @@ def concat(views):
     offs[1:] = np.cumsum([v.n for v in views])
     xyz = np.concatenate([v.xyz for v in views], axis=0) if views else np.zeros((0, 3), np.int32)
     return np.ascontiguousarray(xyz, dtype=np.int32), offs
+
+
+# ---------------------------------------------------------------- raw frames
+#
+# The camera digitises a view of 300 x 250 x 50 um into 1280 x 1024 pixels and
+# 40 frames (Section 2).  Pixel pitch in 10 nm units, as exact fractions:
+# x 30000 / 1280 = 375 / 16, y 25000 / 1024 = 3125 / 128, z 5000 / 40 = 125.
+FRAME_W, FRAME_H, FRAME_D = 1280, 1024, 40
+FRAME_EXTENT = (300 * UM, 250 * UM, 50 * UM)
+PITCH_NUM = (375, 3125, 125)
+PITCH_DEN = (16, 128, 1)
+GRAIN_THRESHOLD = 25
+
+
+@dataclasses.dataclass
+class Frames:
+    raw: np.ndarray      # uint8 [D][H][row_pitch]; grains are dark
+    gain: np.ndarray     # uint8 [H][W] per-pixel gain, 128 = 1.0
+    thr: np.ndarray      # uint8 [H][W] per-pixel threshold
+    width: int
+
+    @property
+    def shape(self):
+        return (self.raw.shape[0], self.raw.shape[1], self.width)
+
+
+def render(px, py, pz, amp, shape, seed, row_pitch=None, psf_xy=1.0, psf_z=0.8, dark=55.0,
+           noise=3.0, col_sigma=0.08, px_sigma=0.03, margin=10, quantum=None):
+    """Raw frames of grains at voxel positions (px, py, pz) with pulse heights amp.
+
+    Each grain is a Gaussian blob (sigma psf_xy pixels, psf_z frames).  A pixel
+    of sensitivity s (column pattern: the vertical lines of a raw frame, plus a
+    per-pixel term) records darkness s * (dark + signal + noise); the raw value
+    is 255 minus that, rounded and clipped.  quantum rounds the darkness to
+    multiples of it first (many equal neighbours).  The calibration returned
+    with the frames: gain = 128 / s and a threshold at the pixel's corrected
+    background plus margin.  Rows are row_pitch >= W bytes; the padding holds
+    random bytes.
+    """
+    D, H, W = shape
+    row_pitch = W if row_pitch is None else int(row_pitch)
+    rng = np.random.default_rng(seed)
+    col = np.clip(rng.standard_normal(W), -2.5, 2.5)
+    s = 1.0 + col_sigma * col[None, :] + px_sigma * np.clip(rng.standard_normal((H, W)), -3.0, 3.0)
+    gain = np.clip(np.rint(128.0 / s), 0, 255).astype(np.uint8)
+    thr = np.clip(np.rint(dark * s * gain / 128.0) + margin, 0, 255).astype(np.uint8)
+
+    sig = np.zeros(D * H * W, dtype=np.float32)
+    px, py, pz = (np.asarray(a, dtype=np.float64) for a in (px, py, pz))
+    amp = np.asarray(amp, dtype=np.float64)
+    if px.size:
+        oz, oy, ox = np.meshgrid(np.arange(-2, 3), np.arange(-3, 4), np.arange(-3, 4), indexing="ij")
+        ox, oy, oz = ox.ravel(), oy.ravel(), oz.ravel()
+        ix = np.rint(px)[:, None].astype(np.int64) + ox[None]
+        iy = np.rint(py)[:, None].astype(np.int64) + oy[None]
+        iz = np.rint(pz)[:, None].astype(np.int64) + oz[None]
+        wgt = amp[:, None] * np.exp(-((ix - px[:, None]) ** 2 + (iy - py[:, None]) ** 2) / (2 * psf_xy ** 2)
+                                    - (iz - pz[:, None]) ** 2 / (2 * psf_z ** 2))
+        ok = (ix >= 0) & (ix < W) & (iy >= 0) & (iy < H) & (iz >= 0) & (iz < D)
+        np.add.at(sig, ((iz * H + iy) * W + ix)[ok], wgt[ok].astype(np.float32))
+    sig = sig.reshape(D, H, W)
+    sig += np.float32(noise) * rng.standard_normal((D, H, W), dtype=np.float32)
+    darkness = s.astype(np.float32)[None] * (np.float32(dark) + sig)
+    if quantum:
+        darkness = np.float32(quantum) * np.rint(darkness / np.float32(quantum))
+    img = np.clip(np.rint(255.0 - darkness), 0, 255).astype(np.uint8)
+    raw = np.empty((D, H, row_pitch), dtype=np.uint8)
+    raw[:, :, :W] = img
+    if row_pitch > W:
+        raw[:, :, W:] = rng.integers(0, 256, (D, H, row_pitch - W), dtype=np.uint8)
+    return Frames(raw=raw, gain=gain, thr=thr, width=W)
+
+
+def frames_view(seed, n_fog=10000, n_through=100, n_short=0, row_pitch=None, amp=(60.0, 110.0)):
+    """One full 1280 x 1024 x 40 view: the grains of make_view on the camera's
+    300 x 250 x 50 um volume, rendered into raw frames.  Returns (View, Frames)."""
+    v = make_view(seed, extent=FRAME_EXTENT, n_fog=n_fog, n_through=n_through, n_short=n_short)
+    rng = np.random.default_rng([seed, 7])
+    xyz = v.xyz.astype(np.float64)
+    px = xyz[:, 0] * PITCH_DEN[0] / PITCH_NUM[0]
+    py = xyz[:, 1] * PITCH_DEN[1] / PITCH_NUM[1]
+    pz = xyz[:, 2] * PITCH_DEN[2] / PITCH_NUM[2]
+    a = rng.uniform(amp[0], amp[1], v.n)
+    fr = render(px, py, pz, a, (FRAME_D, FRAME_H, FRAME_W), seed=[seed, 8], row_pitch=row_pitch)
+    return v, fr
+
+
+def random_blobs(shape, n, seed, row_pitch=None, amp=(40.0, 120.0), **kw):
+    """n grains at uniform random voxel positions of a stack of the given shape."""
+    D, H, W = shape
+    rng = np.random.default_rng(seed)
+    px = rng.uniform(-0.5, W - 0.5, n)
+    py = rng.uniform(-0.5, H - 0.5, n)
+    pz = rng.uniform(-0.5, D - 0.5, n)
+    a = rng.uniform(amp[0], amp[1], n)
+    return render(px, py, pz, a, shape, seed=[seed, 1], row_pitch=row_pitch, **kw)
