@@ -41,7 +41,6 @@ int bits_for(unsigned long long maxval) {
     return b;
 }
 
-static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // ---------------------------------------------------------------- context
 
@@ -80,17 +79,6 @@ void Group::release(Ctx *ctx) {
     bytes = 0;
 }
 
-// Carves consecutive 256-byte aligned slices out of one allocation.
-struct Carver {
-    size_t off = 0;
-    char *base = nullptr;
-    template <class T>
-    T *take(size_t count) {
-        size_t o = off;
-        off = align_up(off + count * sizeof(T), 256);
-        return base ? (T *)(base + o) : nullptr;
-    }
-};
 
 // ---------------------------------------------------------------- parameters
 
@@ -771,21 +759,6 @@ void BatchRT::stats(et_stats *o) {
 // ==================================================================== C ABI
 
 using namespace et;
-
-struct et_ctx : public Ctx {};
-struct et_batch : public BatchRT {
-    using BatchRT::BatchRT;
-};
-
-#define GUARD_BEGIN try {
-#define GUARD_END                                                        \
-    }                                                                    \
-    catch (const std::bad_alloc &) {                                     \
-        return fail(ET_ERR_OOM, "host allocation failed");               \
-    }                                                                    \
-    catch (...) {                                                        \
-        return fail(ET_ERR_CUDA, "unexpected exception in the runtime"); \
-    }
 
 extern "C" {
 

@@ -12,6 +12,21 @@ et_status cuda_fail(cudaError_t e, const char *what);
 et_status check_params(const et_params *p);
 int bits_for(unsigned long long maxval);
 
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Carves consecutive 256-byte aligned slices out of one allocation.
+struct Carver {
+    size_t off = 0;
+    char *base = nullptr;
+    template <class T>
+    T *take(size_t count) {
+        size_t o = off;
+        off = align_up(off + count * sizeof(T), 256);
+        return base ? (T *)(base + o) : nullptr;
+    }
+};
+
+
 struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -117,3 +132,19 @@ struct BatchRT {
 };
 
 }  // namespace et
+
+// Opaque handles of the C ABI.
+struct et_ctx : public et::Ctx {};
+struct et_batch : public et::BatchRT {
+    using et::BatchRT::BatchRT;
+};
+
+#define GUARD_BEGIN try {
+#define GUARD_END                                                        \
+    }                                                                    \
+    catch (const std::bad_alloc &) {                                     \
+        return et::fail(ET_ERR_OOM, "host allocation failed");           \
+    }                                                                    \
+    catch (...) {                                                        \
+        return et::fail(ET_ERR_CUDA, "unexpected exception in the runtime"); \
+    }

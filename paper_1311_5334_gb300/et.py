@@ -10,6 +10,12 @@ The names mirror the C ABI:
     view = ctx.view(xyz, params)          # et_view_create (host grains)
     view.find()                           # et_track_find (async)
     tracks, members = view.fetch()        # et_track_fetch
+
+and of the image front end (include/et_frames.h):
+
+    fr = ctx.frames(frame_params, gain, thr)   # et_frames_create
+    fr.run(raw)                                # et_frames_run (async)
+    xyz, pulse, offsets = fr.fetch()           # et_frames_fetch
 """
 from __future__ import annotations
 
@@ -64,6 +70,20 @@ class Result(C.Structure):
                 ("t_admit_ns", C.c_int64), ("t_done_ns", C.c_int64)]
 
 
+class FrameParams(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("depth", C.c_int32), ("row_pitch", C.c_int32),
+                ("pitch_num", C.c_int32 * 3), ("pitch_den", C.c_int32 * 3), ("grain_threshold", C.c_int32),
+                ("flags", C.c_uint32)]
+
+
+class FramesStats(C.Structure):
+    _fields_ = [("n_views", C.c_int64), ("n_voxels", C.c_int64), ("n_candidates", C.c_int64),
+                ("n_grains", C.c_int64), ("kernel_ms", C.c_float), ("run_ms", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 TRACK_DTYPE = np.dtype([("seed_i", "<i4"), ("seed_j", "<i4"), ("nhits", "<i4"), ("view", "<i4"),
                         ("member_offset", "<i8"), ("c", "<f4", (3,)), ("u", "<f4", (3,)),
                         ("tmin", "<f4"), ("tmax", "<f4"), ("count", "<i4"), ("reserved", "<i4")])
@@ -116,6 +136,16 @@ _SIGS = {
     "et_server_destroy": (C.c_int32, [C.c_void_p]),
     "et_tube_count_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(Params), C.c_void_p, C.c_int64,
                                           C.c_void_p, C.c_void_p]),
+    "et_frames_create": (C.c_int32, [C.c_void_p, C.POINTER(FrameParams), C.c_void_p, C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "et_frames_set_calibration": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "et_frames_run": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
+    "et_frames_sync": (C.c_int32, [C.c_void_p]),
+    "et_frames_fetch": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                    C.POINTER(C.c_int64)]),
+    "et_frames_to_batch": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "et_frames_stats_get": (C.c_int32, [C.c_void_p, C.POINTER(FramesStats)]),
+    "et_frames_destroy": (C.c_int32, [C.c_void_p]),
 }
 
 
@@ -226,6 +256,9 @@ class Context:
 
     def batch(self, params):
         return Batch(self, params)
+
+    def frames(self, frame_params, gain, thr):
+        return Frames(self, frame_params, gain, thr)
 
     def server(self, params, mem_budget_bytes, max_batch_views=256):
         return Server(self, params, mem_budget_bytes, max_batch_views)
@@ -405,6 +438,99 @@ class Server:
         if getattr(self, "_h", None):
             lib().et_server_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def make_frame_params(width, height, depth, pitch_num, pitch_den, grain_threshold, row_pitch=None,
+                      flags=0) -> FrameParams:
+    p = FrameParams()
+    p.width, p.height, p.depth = int(width), int(height), int(depth)
+    p.row_pitch = int(width if row_pitch is None else row_pitch)
+    for k in range(3):
+        p.pitch_num[k] = int(pitch_num[k])
+        p.pitch_den[k] = int(pitch_den[k])
+    p.grain_threshold, p.flags = int(grain_threshold), int(flags)
+    return p
+
+
+class Frames:
+    """et_frames: the image front end of one camera (filtering and 3D grain
+    recognition, Section 2).  gain / thr: uint8 [height][width]."""
+
+    def __init__(self, ctx: Context, frame_params, gain, thr):
+        self.ctx = ctx
+        self.params = frame_params
+        g = np.ascontiguousarray(gain, dtype=np.uint8)
+        t = np.ascontiguousarray(thr, dtype=np.uint8)
+        h = C.c_void_p()
+        _check(lib().et_frames_create(ctx._h, C.byref(self.params), _ptr(g), _ptr(t), C.byref(h)))
+        self._h = h
+        self._keep = None
+        self.n_views = 0
+
+    def set_calibration(self, gain, thr):
+        g = np.ascontiguousarray(gain, dtype=np.uint8)
+        t = np.ascontiguousarray(thr, dtype=np.uint8)
+        _check(lib().et_frames_set_calibration(self._h, _ptr(g), _ptr(t)))
+
+    def run(self, raw, n_views=None, stream=None):
+        """raw: uint8 views back to back (depth x height x row_pitch bytes each),
+        a host array or a CUDA torch tensor (read in place)."""
+        view_bytes = self.params.depth * self.params.height * self.params.row_pitch
+        if hasattr(raw, "is_cuda") and raw.is_cuda:
+            t = raw.contiguous()
+            ptr, on_dev, keep, nbytes = C.c_void_p(t.data_ptr()), 1, t, t.numel() * t.element_size()
+        else:
+            keep = np.ascontiguousarray(raw, dtype=np.uint8)
+            ptr, on_dev, nbytes = _ptr(keep), 0, keep.nbytes
+        if n_views is None:
+            if nbytes % view_bytes:
+                raise ValueError(f"{nbytes} bytes is not a whole number of {view_bytes}-byte views")
+            n_views = nbytes // view_bytes
+        self._keep = keep
+        self.n_views = int(n_views)
+        _check(lib().et_frames_run(self._h, ptr, self.n_views, on_dev, _stream_ptr(stream)))
+
+    def sync(self):
+        _check(lib().et_frames_sync(self._h))
+
+    def fetch(self):
+        """(xyz int32 [n][3], pulse int32 [n], view_offsets int64 [V+1]) in raster
+        order of each view's defining voxels."""
+        n = C.c_int64()
+        st = lib().et_frames_fetch(self._h, None, None, None, 0, C.byref(n))
+        if st not in (OK, CAPACITY):
+            _check(st)
+        xyz = np.zeros((n.value, 3), dtype=np.int32)
+        pulse = np.zeros(n.value, dtype=np.int32)
+        voff = np.zeros(self.n_views + 1, dtype=np.int64)
+        _check(lib().et_frames_fetch(self._h, _ptr(voff), _ptr(xyz), _ptr(pulse), n.value, C.byref(n)))
+        return xyz, pulse, voff
+
+    def to_batch(self, batch, stream=None):
+        _check(lib().et_frames_to_batch(self._h, batch._h, _stream_ptr(stream)))
+        batch.n_views = self.n_views
+
+    def stats(self):
+        s = FramesStats()
+        _check(lib().et_frames_stats_get(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().et_frames_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
     def __enter__(self):
         return self

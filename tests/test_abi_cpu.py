@@ -1,6 +1,6 @@
 """The C ABI without a GPU: libet.so builds, loads, exports every function
-that include/et.h declares, and refuses to run without a CUDA device (no CPU
-fallback).  No compute call is made here."""
+that the headers in include/ declare, and refuses to run without a CUDA
+device (no CPU fallback).  No compute call is made here."""
 import ctypes as C
 import os
 import re
@@ -8,7 +8,8 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "et.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +20,7 @@ def libet():
 
 
 def declared_functions():
-    text = open(HEADER).read()
+    text = "".join(open(h).read() for h in HEADERS)
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(et_[a-z0-9_]+)\s*\(", text)) - {"et_alloc_fn", "et_free_fn"})
 
@@ -27,7 +28,8 @@ def declared_functions():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["et_view_create", "et_track_find", "et_track_fetch", "et_server_submit",
-                     "et_server_poll", "et_batch_find", "et_last_error"]:
+                     "et_server_poll", "et_batch_find", "et_last_error", "et_frames_run", "et_frames_fetch",
+                     "et_frames_to_batch"]:
         assert required in names
 
 
@@ -54,6 +56,8 @@ def test_track_layout_matches_header():
     assert et.TRACK_DTYPE.itemsize == 64
     assert C.sizeof(et.Params) == 32
     assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4 + 4 * 2 + 4 * 6
+    assert C.sizeof(et.FrameParams) == 4 * 4 + 4 * 3 + 4 * 3 + 4 + 4
+    assert C.sizeof(et.FramesStats) == 8 * 4 + 4 * 2
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="a GPU is present")
