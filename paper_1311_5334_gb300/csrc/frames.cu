@@ -6,20 +6,24 @@
 // view and walks its frames front to back.  The frames reach shared memory
 // by TMA (a 3D tensor map over the raw bytes, one box of TX x (TY + 2)
 // pixels per frame: the tile plus one halo row above and below), through a
-// ring of NSTAGE buffers with one mbarrier each, LOOKAHEAD frames ahead.
+// ring of NSTAGE buffers with one mbarrier each.  The block's warps then run
+// independently: each scans its four rows of the tile and, once done with
+// a frame, counts itself out of that frame's stage; the last warp to let go
+// of a stage loads the frame NSTAGE further on into it.  No block-wide
+// barrier is taken inside the frame loop.
 //
 // Filtering is monotone in the raw value (non-increasing), so f > T holds
 // exactly for raw values below a per-pixel cutoff: the count of raw values
 // whose filtered value exceeds T, computed once per calibration by
 // k_cutoff from the same formula.  The scan of a frame therefore compares 16
-// raw bytes per thread against 16 cutoffs held in registers (four byte-wise
-// SIMD compares) and queues the rare candidates in shared memory.  The block
-// then evaluates the queued candidates one per thread: the filtered values
-// of the 3 x 3 x 3 neighbourhood (halo columns outside the tile come from
-// global memory), the maximum test with the raster-order tie rule, and the
-// exact centre of mass in 64-bit integers.  A grain is appended with its key
-// (view, frame, row, column); a radix sort by key then gives every view's
-// grains in raster order, independent of the order blocks ran in.
+// raw bytes per lane against 16 cutoffs held in registers (four byte-wise
+// SIMD compares).  The warp then evaluates its rare candidates one at a time
+// with one neighbour of the 3 x 3 x 3 box per lane (halo columns outside the
+// tile come from global memory): one ballot decides the maximum test with the
+// raster-order tie rule (lanes are in raster order, the candidate is lane 13),
+// warp reductions give the exact centre-of-mass sums.  A grain is appended
+// with its key (view, frame, row, column); a radix sort by key then gives
+// every view's grains in raster order, independent of the order blocks ran in.
 #include <cuda.h>
 
 #include <cstring>
@@ -32,12 +36,18 @@ namespace et {
 
 namespace {
 
-constexpr int TX = 128, TY = 32, FT = 256;
-constexpr int NSTAGE = 6, LOOKAHEAD = NSTAGE - 2;
+constexpr int TX = 256, TY = 16, FT = 256;
+constexpr int LPR = TX / 16;              // lanes per tile row (16 pixels each)
+constexpr int RPW = 32 / LPR;             // tile rows per warp
+constexpr int NSTAGE = 6;
 constexpr int STAGE_BYTES = TX * (TY + 2);
-constexpr int HX = TX + 2, HY = TY + 2;   // calibration tile with a one-pixel halo
-static_assert(FT == (TX / 16) * TY, "one thread per 16 pixels of the tile");
+// calibration tile: the pixel tile with one halo row above and below and 16
+// columns on either side (so that it loads as aligned 16-byte vectors); pixel
+// column lx of the tile is calibration column lx + 16
+constexpr int HX = TX + 32, HY = TY + 2;
+static_assert(FT == LPR * TY, "one thread per 16 pixels of the tile");
 static_assert(STAGE_BYTES % 128 == 0, "stage buffers stay 128-byte aligned");
+static_assert(TX <= 256 && TY + 2 <= 256, "TMA box edges are at most 256 elements");
 
 enum : u32 { FRB_OVF = 1u << 0, FRB_TIMEOUT = 1u << 1 };
 
@@ -54,7 +64,8 @@ struct FrArgs {
     int num[3], den[3];
     int tiles_x;
     const unsigned char *raw;   // device copy of the views (halo columns of candidates)
-    const unsigned char *gain, *thr, *cut;
+    const unsigned char *gain, *thr, *cut;   // padded tables: pixel (x, y) at (y + 1) * TP + x + 16
+    int TP;
     FrCtl *ctl;
     u64 *keys;
     u32 *vals;
@@ -89,39 +100,50 @@ __device__ __forceinline__ u64 global_ns() {
 
 // Waits for the phase `parity` of the mbarrier at bar; false after about a
 // second without completion (the caller records a timeout and leaves).
-__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
+__device__ __forceinline__ bool mbar_try(u32 bar, u32 parity) {
+    u32 done;
+    // suspends for up to 2 us while the phase is pending instead of spinning
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "r"(2000)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __noinline__ bool mbar_wait_slow(u32 bar, u32 parity) {
     const u64 t0 = global_ns();
     for (u32 it = 0;; ++it) {
-        u32 done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((it & 63) == 63 && global_ns() - t0 > 1000000000ull) return false;
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 7) == 7 && global_ns() - t0 > 1000000000ull) return false;
         if (it > (1u << 26)) return false;
     }
 }
 
-__global__ void __launch_bounds__(FT) k_recognize(const __grid_constant__ CUtensorMap tmap, FrArgs a) {
-    __shared__ __align__(128) unsigned char stage[NSTAGE][STAGE_BYTES];
-    __shared__ unsigned char gsm[HY][HX], tsm[HY][HX];
-    __shared__ unsigned short queue[TX * TY];
-    __shared__ __align__(8) u64 mbar[NSTAGE];
-    __shared__ int qn[2];
+// Waits for the phase `parity` of the mbarrier at bar; false after about a
+// second without completion (the caller records a timeout and leaves).
+__device__ __forceinline__ bool mbar_wait(u32 bar, u32 parity) {
+    return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
+}
 
-    const int tid = threadIdx.x;
+__global__ void __launch_bounds__(FT, 5) k_recognize(const __grid_constant__ CUtensorMap tmap, FrArgs a) {
+    __shared__ __align__(128) unsigned char stage[NSTAGE][STAGE_BYTES];
+    __shared__ __align__(16) unsigned char gsm[HY][HX];
+    __shared__ __align__(16) unsigned char tsm[HY][HX];
+    __shared__ __align__(8) u64 mbar[NSTAGE];
+    __shared__ int released[NSTAGE];   // warps done with the frame a stage holds
+    __shared__ int issued;             // frames whose load has been issued
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int v = blockIdx.y;
     const int x0 = (blockIdx.x % a.tiles_x) * TX, y0 = (blockIdx.x / a.tiles_x) * TY;
     const int D = a.D;
 
-    auto issue = [&](int j) {   // TMA of frame j of this view into its stage
-        const int s = j % NSTAGE;
+    auto issue = [&](int j, int s) {   // TMA of frame j of this view into stage s = j % NSTAGE
         const u32 bar = smem_addr(&mbar[s]);
-        // the stage was last read by ordinary loads (before a block barrier)
+        // the stage was last read by ordinary loads of every warp (released below)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(STAGE_BYTES)
                      : "memory");
@@ -133,138 +155,217 @@ __global__ void __launch_bounds__(FT) k_recognize(const __grid_constant__ CUtens
     };
 
     if (tid == 0) {
-        for (int s = 0; s < NSTAGE; ++s)
+        for (int s = 0; s < NSTAGE; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[s])) : "memory");
+            released[s] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        qn[0] = qn[1] = 0;
+        issued = min(D, NSTAGE);
     }
     __syncthreads();
-    int issued = 0, last_z = 0;   // frames issued (thread 0), step reached
     if (tid == 0)
-        for (; issued < min(D, LOOKAHEAD); ++issued) issue(issued);
+        for (int j = 0; j < min(D, NSTAGE); ++j) issue(j, j);
 
-    // calibration of the tile and its halo (pixels outside the frame: 0)
-    for (int i = tid; i < HY * HX; i += FT) {
-        const int ly = i / HX, lx = i % HX;
-        const int gy = y0 + ly - 1, gx = x0 + lx - 1;
-        const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-        gsm[ly][lx] = in ? a.gain[(size_t)gy * a.W + gx] : 0;
-        tsm[ly][lx] = in ? a.thr[(size_t)gy * a.W + gx] : 0;
+    // calibration of the tile with its halo and margins (zero outside the frame)
+    for (int i = tid; i < HY * (HX / 16); i += FT) {
+        const int row = i / (HX / 16), c16 = (i % (HX / 16)) * 16;
+        const size_t off = (size_t)(y0 + row) * a.TP + x0 + c16;
+        *(uint4 *)&gsm[row][c16] = __ldg((const uint4 *)(a.gain + off));
+        *(uint4 *)&tsm[row][c16] = __ldg((const uint4 *)(a.thr + off));
     }
-    // this thread's 16 pixels: row ry of the tile, columns cx .. cx + 15
-    const int ry = tid / (TX / 16), cx = (tid % (TX / 16)) * 16;
-    u32 cw[4];
+    // this lane's 16 pixels: row ry of the tile (warp w scans rows RPW w ..
+    // RPW w + RPW - 1), columns cx .. cx + 15, and their cutoffs
+    const int ry = tid / LPR, cx = (tid % LPR) * 16;
+    u32 cw[4];   // cutoffs of the 16 pixels, 4 per word, low 7 bits of each byte
+    u32 ch[4];   // and their high bits
     {
-        const int gy = y0 + ry;
+        const uint4 c = __ldg((const uint4 *)(a.cut + (size_t)(y0 + ry + 1) * a.TP + x0 + cx + 16));
+        const u32 cv[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            u32 wv = 0;
-#pragma unroll
-            for (int bb = 0; bb < 4; ++bb) {
-                const int gx = x0 + cx + 4 * k + bb;
-                const u32 c = (gy < a.H && gx < a.W) ? a.cut[(size_t)gy * a.W + gx] : 0u;
-                wv |= c << (8 * bb);
-            }
-            cw[k] = wv;
+            cw[k] = cv[k] & 0x7f7f7f7fu;
+            ch[k] = cv[k] & 0x80808080u;
         }
     }
-    __syncthreads();
+    __syncthreads();   // calibration tiles complete; from here on the warps run independently
 
+    // this lane's neighbour in a candidate's 3 x 3 x 3 box (lanes 0..26, raster
+    // order, so lane 13 is the candidate and lanes below it come before it)
+    const int ndz = lane / 9 - 1, ndy = (lane / 3) % 3 - 1, ndx = lane % 3 - 1;
+    // the centroid coordinate this lane computes for a grain (lanes 0, 1, 2)
+    const int cnum = lane == 0 ? a.num[0] : (lane == 1 ? a.num[1] : a.num[2]);
+    const int cden = lane == 0 ? a.den[0] : (lane == 1 ? a.den[1] : a.den[2]);
     u32 ncand = 0;
+    u32 fprev[4] = {0u, 0u, 0u, 0u};
     bool timed_out = false;
-    for (int z = 0; z < D; ++z) {
-        last_z = z;
-        if (tid == 0 && z + LOOKAHEAD < D) issue(issued++);   // frame z + LOOKAHEAD; its stage held frame z - 2
-        bool ok = true;
-        if (z == 0) ok = mbar_wait(smem_addr(&mbar[0]), 0);
-        if (ok && z + 1 < D) ok = mbar_wait(smem_addr(&mbar[(z + 1) % NSTAGE]), ((z + 1) / NSTAGE) & 1);
-        if (tid == 0) qn[(z + 1) & 1] = 0;
-        if (__syncthreads_or(!ok)) {
+    // stages of frames z - 1, z, z + 1 and the phase parity of frame z + 1
+    int sm1 = NSTAGE - 1, s0 = 0, sp1 = 1;
+    u32 par1 = 0;
+    if (!mbar_wait(smem_addr(&mbar[0]), 0)) timed_out = true;
+    for (int z = 0; z < D && !timed_out; ++z) {
+        if (z + 1 < D && !mbar_wait(smem_addr(&mbar[sp1]), par1)) {
             timed_out = true;
             break;
         }
-        // scan: queue the pixels of frame z whose raw value is below the cutoff
-        const unsigned char *f0 = stage[z % NSTAGE];
+        // scan: this lane's pixels of frame z whose raw value is below the cutoff
+        const unsigned char *f0 = stage[s0];
         const uint4 rw = *(const uint4 *)&f0[(ry + 1) * TX + cx];
-        const u32 m[4] = {__vcmpltu4(rw.x, cw[0]), __vcmpltu4(rw.y, cw[1]), __vcmpltu4(rw.z, cw[2]),
-                          __vcmpltu4(rw.w, cw[3])};
-        if (m[0] | m[1] | m[2] | m[3]) {
+        // per byte raw < cutoff, four bytes a word (SWAR): with the byte's high
+        // bits ra, ca and d = (raw | 0x80) - (cutoff & 0x7f) (no borrow between
+        // bytes), raw < cutoff iff (!ra & ca) | (ra == ca & !d7)
+        const u32 rwv[4] = {rw.x, rw.y, rw.z, rw.w};
+        u32 lt[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const u32 d = (rwv[k] | 0x80808080u) - cw[k];
+            lt[k] = ((~rwv[k] & ch[k]) | (~(rwv[k] ^ ch[k]) & ~d)) & 0x80808080u;
+        }
+        u32 bits = 0;   // bit k: pixel cx + k
+        if (lt[0] | lt[1] | lt[2] | lt[3]) {
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                u32 mk = m[k] & 0x01010101u;
-                while (mk) {
-                    const int bb = (__ffs(mk) - 1) >> 3;
-                    mk &= mk - 1;
-                    const int slot = atomicAdd(&qn[z & 1], 1);
-                    queue[slot] = (unsigned short)(((cx + 4 * k + bb) << 5) | ry);
-                }
+                const u32 m = lt[k] >> 7;   // bits 0, 8, 16, 24
+                bits |= ((m & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << (4 * k);
             }
         }
-        __syncthreads();
-        const int nq = qn[z & 1];
-        ncand += tid == 0 ? (u32)nq : 0u;
-        const unsigned char *fm = stage[(z + NSTAGE - 1) % NSTAGE], *fp1 = stage[(z + 1) % NSTAGE];
-        for (int i = tid; i < nq; i += FT) {
-            const int lx = queue[i] >> 5, ly = queue[i] & 31;
-            const int gx = x0 + lx, gy = y0 + ly;
-            const int fpv = filt(f0[(ly + 1) * TX + lx], gsm[ly + 1][lx + 1], tsm[ly + 1][lx + 1]);
-            long long S = 0, SX = 0, SY = 0, SZ = 0;
-            bool is_max = true;
-            for (int dz = -1; dz <= 1 && is_max; ++dz) {
-                const int zz = z + dz;
-                if (zz < 0 || zz >= D) continue;
-                const unsigned char *fr = dz < 0 ? fm : (dz == 0 ? f0 : fp1);
-                for (int dy = -1; dy <= 1 && is_max; ++dy) {
-                    const int yy = gy + dy;
-                    if (yy < 0 || yy >= a.H) continue;
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int xx = gx + dx;
-                        if (xx < 0 || xx >= a.W) continue;
-                        const int lxx = lx + dx;
-                        const int r = (lxx >= 0 && lxx < TX)
-                                          ? fr[(ly + dy + 1) * TX + lxx]
-                                          : __ldg(&a.raw[(((size_t)v * D + zz) * a.H + yy) * (size_t)a.P + xx]);
-                        const int fq = filt(r, gsm[ly + dy + 1][lxx + 1], tsm[ly + dy + 1][lxx + 1]);
-                        const bool before = dz < 0 || (dz == 0 && (dy < 0 || (dy == 0 && dx < 0)));
-                        if (before ? fq >= fpv : fq > fpv) {
-                            is_max = false;
-                            break;
-                        }
-                        S += fq;
-                        SX += (long long)fq * xx;
-                        SY += (long long)fq * yy;
-                        SZ += (long long)fq * zz;
+        // exact pruning inside the lane, before the warp-wide test: filtered
+        // values of the lane's candidates (only candidates can beat a
+        // candidate: every other voxel has f <= T).  Of two candidates next to
+        // each other in x, the earlier loses iff the later is brighter, else
+        // the later loses; a candidate loses to the same pixel one frame back
+        // if that was at least as bright.  fprev: this lane's filtered values
+        // of frame z - 1 (candidates only, else 0), a byte per pixel.
+        u32 fnow[4] = {0u, 0u, 0u, 0u};
+        if (bits) {
+            ncand += __popc(bits);
+            u32 keep = bits, b = bits;
+            int pk = -2, pf = 0;
+            while (b) {
+                const int k = __ffs(b) - 1;
+                b &= b - 1;
+                const int wsel = k >> 2, sh = 8 * (k & 3);
+                const u32 word = wsel == 0 ? rwv[0] : (wsel == 1 ? rwv[1] : (wsel == 2 ? rwv[2] : rwv[3]));
+                const u32 prev = wsel == 0 ? fprev[0] : (wsel == 1 ? fprev[1] : (wsel == 2 ? fprev[2] : fprev[3]));
+                const int f = filt((word >> sh) & 0xffu, gsm[ry + 1][cx + k + 16], tsm[ry + 1][cx + k + 16]);
+                if ((int)((prev >> sh) & 0xffu) >= f) keep &= ~(1u << k);
+                if (pk == k - 1) {
+                    if (pf >= f) keep &= ~(1u << k);
+                    else keep &= ~(1u << pk);
+                }
+                pk = k;
+                pf = f;
+                const u32 ins = (u32)f << sh;
+                fnow[0] |= wsel == 0 ? ins : 0u;
+                fnow[1] |= wsel == 1 ? ins : 0u;
+                fnow[2] |= wsel == 2 ? ins : 0u;
+                fnow[3] |= wsel == 3 ? ins : 0u;
+            }
+            bits = keep;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fprev[k] = fnow[k];
+        unsigned pend = __ballot_sync(0xffffffffu, bits != 0);
+        if (pend) {
+            // per frame: this lane's neighbour (frame, and offsets in the stage and
+            // calibration tiles) and whether its frame exists
+            const int zz = z + ndz;
+            const bool zin = lane < 27 && zz >= 0 && zz < D;
+            const unsigned char *fr = stage[ndz < 0 ? sm1 : (ndz == 0 ? s0 : sp1)] + ndy * TX + ndx;
+            // the warp evaluates its candidates one at a time, a neighbour per lane
+            for (; pend; pend = __ballot_sync(0xffffffffu, bits != 0)) {
+                const int src = __ffs(pend) - 1;
+                const int k = __ffs(__shfl_sync(0xffffffffu, bits, src)) - 1;
+                if (lane == src) bits &= bits - 1;
+                const int lx = (src % LPR) * 16 + k, ly = warp * RPW + src / LPR;   // uniform
+                const int gx = x0 + lx, gy = y0 + ly;
+                const bool in = zin && (unsigned)(gy + ndy) < (unsigned)a.H && (unsigned)(gx + ndx) < (unsigned)a.W;
+                const int sb = (ly + 1) * TX + lx;
+                int r = 0;
+                if (lx > 0 && lx < TX - 1) {   // uniform: the whole box is in the stage
+                    if (in) r = fr[sb];
+                } else if (in) {               // tile edge: halo columns from global memory
+                    r = ((unsigned)(lx + ndx) < (unsigned)TX)
+                            ? fr[sb]
+                            : __ldg(&a.raw[(((size_t)v * D + zz) * a.H + gy + ndy) * (size_t)a.P + gx + ndx]);
+                }
+                const int cb = (ly + 1 + ndy) * HX + lx + ndx + 16;
+                const int fq = in ? filt(r, (&gsm[0][0])[cb], (&tsm[0][0])[cb]) : -1;
+                const int fpv = __shfl_sync(0xffffffffu, fq, 13);
+                const bool beats = lane < 13 ? fq >= fpv : fq > fpv;
+                if (__ballot_sync(0xffffffffu, beats)) continue;   // not a local maximum
+                // centre-of-mass sums, two per reduction: S (< 2^13) below
+                // Sx = sum w dx above; Sy + 4096 (sum of w dy + 128 over 32 lanes, in
+                // [1801, 6391]) below Sz = sum w dz above
+                const int w = max(fq, 0);
+                const int p1 = __reduce_add_sync(0xffffffffu, (u32)(w + ndx * w * 65536));
+                const int p2 = __reduce_add_sync(0xffffffffu, (u32)(ndy * w + 128 + ndz * w * 65536));
+                const int S = p1 & 0xffff, SXo = (p1 - S) >> 16;
+                const int SYo = (p2 & 0xffff) - 4096, SZo = (p2 - (p2 & 0xffff)) >> 16;
+                // coordinate of axis `lane` (lanes 0..2), rounded half up:
+                // floor((2 S g num + 2 So num + S den) / (2 S den)) with the voxel
+                // index g and So the offset sum.  With A = 2 g num = a1 (2 den) + a0
+                // it is a1 + floor((S a0 + 2 So num + S den) / (2 S den)), all in
+                // int32: A < 2^30, S a0 < 9.1e8, |2 So num| < 3.1e8, S den < 4.6e8
+                int c = 0;
+                if (lane < 3) {
+                    const int g = lane == 0 ? gx : (lane == 1 ? gy : z);
+                    const int So = lane == 0 ? SXo : (lane == 1 ? SYo : SZo);
+                    const int A = 2 * g * cnum, twoden = 2 * cden;
+                    const int a1 = A / twoden, a0 = A - a1 * twoden;
+                    const int n = S * a0 + 2 * So * cnum + S * cden, Q = S * twoden;
+                    int q = n / Q;
+                    if (n < 0 && q * Q != n) --q;
+                    c = a1 + q;
+                }
+                const int Y = __shfl_sync(0xffffffffu, c, 1), Z = __shfl_sync(0xffffffffu, c, 2);
+                if (lane == 0) {
+                    const u64 slot = atomicAdd(&a.ctl->n_grains, 1ull);
+                    if (slot < a.cap) {
+                        a.keys[slot] = (u64)v * ((u64)D * a.H * a.W) + ((u64)z * a.H + gy) * a.W + gx;
+                        a.vals[slot] = (u32)slot;
+                        a.rec[slot] = make_int4(c, Y, Z, S);
+                    } else {
+                        atomicOr(&a.ctl->error, FRB_OVF);
                     }
+                    atomicAdd(&a.view_count[v], 1u);
                 }
             }
-            if (!is_max) continue;
-            // centre of mass in coordinate units, rounded half up (all terms positive)
-            const int X = (int)((2 * SX * a.num[0] + S * a.den[0]) / (2 * S * a.den[0]));
-            const int Y = (int)((2 * SY * a.num[1] + S * a.den[1]) / (2 * S * a.den[1]));
-            const int Z = (int)((2 * SZ * a.num[2] + S * a.den[2]) / (2 * S * a.den[2]));
-            const u64 slot = atomicAdd(&a.ctl->n_grains, 1ull);
-            if (slot < a.cap) {
-                a.keys[slot] = (u64)v * ((u64)D * a.H * a.W) + ((u64)z * a.H + gy) * a.W + gx;
-                a.vals[slot] = (u32)slot;
-                a.rec[slot] = make_int4(X, Y, Z, (int)S);
-            } else {
-                atomicOr(&a.ctl->error, FRB_OVF);
+        }
+        // frame z - 1 is no longer needed by this warp; the last warp to let go
+        // of it reloads its stage with frame z + NSTAGE - 1
+        __syncwarp();
+        if (lane == 0 && z >= 1) {
+            __threadfence_block();
+            if (atomicAdd(&released[sm1], 1) == FT / 32 - 1) {
+                released[sm1] = 0;
+                __threadfence_block();
+                const int j = z - 1 + NSTAGE;
+                if (j < D) {
+                    issue(j, sm1);
+                    atomicAdd(&issued, 1);
+                }
             }
-            atomicAdd(&a.view_count[v], 1u);
         }
-        __syncthreads();   // stage z - 1 and the queue are reused from here on
-    }
-    if (timed_out) {
-        // record the failure, then give the copies still in flight into this
-        // block's buffers a bounded chance to land before the block exits
-        if (tid == 0) {
-            atomicOr(&a.ctl->error, FRB_TIMEOUT);
-            for (int j = max(0, last_z); j < issued; ++j)
-                if (!mbar_wait(smem_addr(&mbar[j % NSTAGE]), (j / NSTAGE) & 1)) break;
+        sm1 = s0;
+        s0 = sp1;
+        if (++sp1 == NSTAGE) {
+            sp1 = 0;
+            par1 ^= 1u;
         }
-        return;
     }
-    if (tid == 0 && ncand) atomicAdd(&a.ctl->n_cand, (u64)ncand);
+    ncand = __reduce_add_sync(0xffffffffu, ncand);
+    if (lane == 0 && ncand) atomicAdd(&a.ctl->n_cand, (u64)ncand);
+    if (timed_out && lane == 0) {
+        // record the failure; the block's first warp then gives the copies still
+        // in flight into its buffers a bounded chance to land before it exits
+        atomicOr(&a.ctl->error, FRB_TIMEOUT);
+    }
+    __syncthreads();
+    if (tid == 0 && (*(volatile u32 *)&a.ctl->error & FRB_TIMEOUT)) {
+        const int n = *(volatile int *)&issued;
+        for (int j = max(0, n - NSTAGE); j < n; ++j)
+            if (!mbar_wait(smem_addr(&mbar[j % NSTAGE]), (j / NSTAGE) & 1)) break;
+    }
 }
 
 // Grains in key order: xyz (int32 [n][3]) and pulse (int32 [n]).
@@ -317,7 +418,7 @@ struct FramesRT {
     int *xyz = nullptr, *pulse = nullptr;
     u32 *view_count = nullptr, *view_off = nullptr;
     void *temp = nullptr;
-    int sorted = 0;
+    int sorted = 0, launches = 0;
     cudaStream_t run_stream = nullptr;
     cudaEvent_t ev[4] = {};   // run start, kernel start, kernel end, done
     cudaEvent_t handoff = nullptr;   // a batch's copy of the grains (et_frames_to_batch)
@@ -341,6 +442,12 @@ struct FramesRT {
     }
 
     size_t pixels() const { return (size_t)p.width * p.height; }
+    // padded calibration tables: pitch covering every tile plus 16-byte margins,
+    // one row above and enough below for the last tile's halo
+    int tiles_x() const { return (p.width + TX - 1) / TX; }
+    int tiles_y() const { return (p.height + TY - 1) / TY; }
+    int table_pitch() const { return tiles_x() * TX + 32; }
+    size_t table_bytes() const { return (size_t)table_pitch() * ((size_t)tiles_y() * TY + 2); }
     size_t view_bytes() const { return (size_t)p.depth * p.height * p.row_pitch; }
 
     et_status init() {
@@ -348,10 +455,11 @@ struct FramesRT {
             if (cudaEventCreate(&e) != cudaSuccess) return fail(ET_ERR_CUDA, "event creation failed");
         if (cudaEventCreateWithFlags(&handoff, cudaEventDisableTiming) != cudaSuccess)
             return fail(ET_ERR_CUDA, "event creation failed");
-        if (!g_tab.reserve(ctx, 3 * align_up(pixels(), 256))) return fail(ET_ERR_OOM, "calibration tables");
+        const size_t tb = align_up(table_bytes(), 256);
+        if (!g_tab.reserve(ctx, 3 * tb)) return fail(ET_ERR_OOM, "calibration tables");
         gain = (unsigned char *)g_tab.base;
-        thr = gain + align_up(pixels(), 256);
-        cut = thr + align_up(pixels(), 256);
+        thr = gain + tb;
+        cut = thr + tb;
         if (!g_ctl.reserve(ctx, sizeof(FrCtl))) return fail(ET_ERR_OOM, "control block");
         ctl = (FrCtl *)g_ctl.base;
         return ET_OK;
@@ -360,10 +468,15 @@ struct FramesRT {
     et_status calibrate(const unsigned char *hg, const unsigned char *ht) {
         if (ran) cudaEventSynchronize(ev[3]);
         cudaStream_t st = ctx->stream;
-        cudaError_t e = cudaMemcpyAsync(gain, hg, pixels(), cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(thr, ht, pixels(), cudaMemcpyHostToDevice, st);
+        const size_t tp = (size_t)table_pitch();
+        cudaError_t e = cudaMemsetAsync(gain, 0, 2 * align_up(table_bytes(), 256), st);   // gain and thr
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(gain + tp + 16, tp, hg, p.width, p.width, p.height, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(thr + tp + 16, tp, ht, p.width, p.width, p.height, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "calibration upload");
-        const int n = (int)pixels();
+        // zero gain outside the frame gives a zero cutoff there
+        const int n = (int)table_bytes();
         k_cutoff<<<std::min((n + 255) / 256, 152 * 8), 256, 0, st>>>(gain, thr, cut, n, p.grain_threshold);
         e = cudaStreamSynchronize(st);   // the caller may free its tables on return
         return e == cudaSuccess ? ET_OK : cuda_fail(e, "cutoff table");
@@ -423,6 +536,7 @@ struct FramesRT {
         a.gain = gain;
         a.thr = thr;
         a.cut = cut;
+        a.TP = table_pitch();
         a.ctl = ctl;
         a.keys = keys[0];
         a.vals = vals[0];
@@ -435,6 +549,9 @@ struct FramesRT {
         const int bits = bits_for((u64)V * p.depth * p.height * p.width - 1);
         sorted = radix_sort_pairs_dev(keys[0], vals[0], keys[1], vals[1], (long long)cap, &ctl->n_grains, bits,
                                       temp, st);
+        // recognition, per 8-bit sort pass a histogram, a 3-kernel scan and a
+        // scatter, the gather and the 3-kernel scan of the view counts
+        launches = 1 + 5 * ((bits + 7) / 8) + 1 + 3;
         k_fr_gather<<<152 * 4, 256, 0, st>>>(ctl, cap, vals[sorted], rec, xyz, pulse);
         exclusive_scan_u32(view_count, view_off, (long long)V, temp, st);   // view_off[V] = total
         cudaError_t e = cudaGetLastError();
@@ -636,6 +753,7 @@ et_status et_frames_stats_get(et_frames *fr, et_frames_stats *out) {
     out->n_grains = (int64_t)fr->n_grains();
     out->kernel_ms = fr->kernel_ms;
     out->run_ms = fr->run_ms;
+    out->kernel_launches = fr->launches;
     return ET_OK;
 }
 
