@@ -45,6 +45,10 @@ OPS_PER_TEST = 14
 # dram__bytes_write.sum of one ncu capture on the dense view: 21.96 MB for
 # 2,571,392 seeds); a launch's traffic is scaled by its seed count.
 TUBE_DRAM_BYTES_PER_SEED = (21.964032e6 + 256) / 2571392
+# DRAM bytes of the front end's recognition kernel per view of raw frames
+# (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
+# 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
+FRAMES_DRAM_BYTES_PER_VIEW = (430.692608e6 + 6.068480e6) / 8
 
 
 def dist_env():
@@ -125,7 +129,14 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+FRAMES_VIEWS, FRAMES_DISTINCT = 64, 4
+FRAMES_WORKLOAD = (f"frames: {FRAMES_VIEWS} views of raw camera frames 1280x1024x40 (300x250x50 um, 8-bit, grains "
+                   f"dark), {FRAMES_DISTINCT} distinct rendered views repeated (each 10k fog grains + 100 isotropic "
+                   "tracks, Gaussian PSF 1.0 px / 0.8 frame, pulse 60-110, column and pixel gain pattern, noise 3), "
+                   "one camera calibration, grain threshold 25, seeds 200-203, camera seed 1")
+
 WORKLOADS = {
+    "frames": FRAMES_WORKLOAD,
     "batched": WORKLOAD,
     "dense": ("dense: one view 300x300x50 um, 20,000 fog + 200 isotropic through-going tracks (gaps 3.3 um) "
               "+ 100 short tracks (range 10-50 um, gaps 1.6 um), jitter 0.05/0.3 um, int32 10 nm coords, "
@@ -428,6 +439,222 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws):
     return plain_views_per_s, e2e_val, h2d, d2h
 
 
+
+# ---------------------------------------------------------------------------- image front end
+
+def make_frames_workload():
+    """FRAMES_DISTINCT rendered views (one camera) and the shared calibration."""
+    frs = [synth.frames_view(200 + k, n_fog=10000, n_through=100, camera_seed=1)[1]
+           for k in range(FRAMES_DISTINCT)]
+    return frs, frs[0].gain, frs[0].thr
+
+
+def oracle_frames_per_s(frs, gain, thr, budget_s):
+    """Times the oracle (filter + grain recognition) on the distinct views, cycled."""
+    from oracle import oracle as O
+    O.build()
+    done, t_used, grains = 0, 0.0, 0
+    while t_used < budget_s:
+        fr = frs[done % len(frs)]
+        t0 = time.perf_counter()
+        f = O.frames_filter(fr.raw, gain, thr)
+        g = O.frames_grains(f, synth.GRAIN_THRESHOLD, synth.PITCH_NUM, synth.PITCH_DEN)
+        t_used += time.perf_counter() - t0
+        grains += len(g[0])
+        done += 1
+    return done, t_used, grains
+
+
+def run_frames_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    frs, gain, thr = make_frames_workload()
+    per_step = max(1.0, float(os.environ.get("ET_REF_STEP_S", "4")))
+    for _ in range(args.warmup):
+        oracle_frames_per_s(frs, gain, thr, per_step / 4)
+    tot_v, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        d, t, _ = oracle_frames_per_s(frs, gain, thr, per_step)
+        tot_v += d
+        tot_t += t
+    value = tot_v / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": FRAMES_WORKLOAD, "parallelism": "oracle on one host core"},
+            "cpu_baseline": {"value": value, "unit": "views/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{tot_v} views (the {FRAMES_DISTINCT} distinct views cycled), "
+                                       f"~{per_step:.0f} s per step, filter + recognition single-threaded"},
+            "e2e": {"value": value, "unit": "views/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_frames(args):
+    import torch
+    from paper_1311_5334_gb300 import et
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    frs, gain, thr = make_frames_workload()
+    D, H, P = frs[0].raw.shape
+    W = frs[0].width
+    V = args.frames_views
+    view_bytes = D * H * P
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = et.Context(local)
+    distinct = [torch.from_numpy(fr.raw.reshape(-1)).cuda() for fr in frs]
+    raw_d = torch.empty(V * view_bytes, dtype=torch.uint8, device="cuda")
+    for k in range(V):
+        raw_d[k * view_bytes:(k + 1) * view_bytes].copy_(distinct[k % len(distinct)])
+    del distinct
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fp = et.make_frame_params(W, H, D, synth.PITCH_NUM, synth.PITCH_DEN, synth.GRAIN_THRESHOLD, row_pitch=P)
+    fr = et.Frames(ctx, fp, gain, thr)
+
+    def step():
+        fr.run(raw_d, n_views=V, stream=stream)
+
+    for _ in range(max(args.warmup, 1)):
+        step()
+        fr.sync()
+        flush.zero_()
+    ref = fr.stats()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    t_wall0 = time.perf_counter()
+    step_ms, kern_ms = [], []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        fr.sync()
+        st = fr.stats()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(st["kernel_ms"])
+        assert st["n_grains"] == ref["n_grains"]
+        flush.zero_()
+    barrier()
+    wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    total_ms = reduce_max(float(np.sum(step_ms)), dist, device="cuda")
+    ms_per_step = total_ms / args.steps
+    value = whole_job_rate(V, ws, ms_per_step)
+
+    # roofline of the recognition kernel: HBM.  Algorithmic bytes per launch:
+    # the raw frames read once, the three per-pixel tables read once, and per
+    # grain a sort key (8 B), an index (4 B) and a record (16 B) written.
+    k_ms = float(np.mean(kern_ms))
+    alg_bytes = V * view_bytes + 3 * H * W + 28 * ref["n_grains"]
+    achieved = alg_bytes / (k_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+
+    extra = {}
+    if not args.no_extra:
+        extra = frames_extras(args, ctx, fp, frs, gain, thr, raw_d, V, view_bytes, stream, ws)
+    line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": FRAMES_WORKLOAD.replace(f"{FRAMES_VIEWS} views", f"{V} views"),
+                       "views_per_step": V, "bytes_per_step": V * view_bytes,
+                       "voxels_per_step": ref["n_voxels"], "candidates_per_step": ref["n_candidates"],
+                       "grains_per_step": ref["n_grains"],
+                       "l2": "inputs (3.4 GB) larger than L2; also flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas: one {V}-view batch per rank x {ws}"},
+            "kernel_ms": k_ms,
+            "wall_s": wall,
+            "roofline": {"bound": "hbm", "kernel": "k_recognize", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": FRAMES_DRAM_BYTES_PER_VIEW * V if FRAMES_DRAM_BYTES_PER_VIEW else None,
+                         "basis": f"{alg_bytes / 1e9:.3f} GB per launch (raw frames once, tables once, "
+                                  f"28 B per grain written) / {k_ms:.3f} ms (CUDA events); peak {peak_src} "
+                                  "copy bandwidth"},
+            "gpu_launches": int(ref["kernel_launches"]) * args.steps,
+            "clocks": clk}
+    line.update(extra)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra:
+        budget = float(os.environ.get("ET_CPU_BASELINE_S", "15"))
+        d, t, _ = oracle_frames_per_s(frs, gain, thr, budget)
+        line["cpu_baseline"] = {"value": d / t, "unit": "views/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{d} views (the {FRAMES_DISTINCT} distinct views cycled), {t:.1f} s, "
+                                          "filter + recognition single-threaded"}
+    fr.close()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def frames_extras(args, ctx, fp, frs, gain, thr, raw_d, V, view_bytes, stream, ws):
+    """End to end from pinned host frames to host grains, and the chain from
+    raw frames to tracks on the device."""
+    import torch
+    from paper_1311_5334_gb300 import et
+    pinned = torch.empty(V * view_bytes, dtype=torch.uint8).pin_memory()
+    pinned.copy_(raw_d.cpu())
+    host = pinned.numpy()
+    fr = et.Frames(ctx, fp, gain, thr)
+    fr.run(host, n_views=V)
+    xyz, pulse, voff = fr.fetch()
+    steps = max(3, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        fr.run(host, n_views=V)
+        xyz, pulse, voff = fr.fetch()
+    e2e_s = (time.perf_counter() - t0) / steps
+    d2h = xyz.nbytes + pulse.nbytes + voff.nbytes + 64
+
+    # frames -> grains -> tracks, device resident (one track-finding batch of V views)
+    params = synth.params(synth.FRAME_EXTENT)
+    b = et.Batch(ctx, params)
+    b.set_tuning((150, 600, 600), row_lists=1)
+
+    def chain():
+        fr.run(raw_d, n_views=V, stream=stream)
+        fr.to_batch(b, stream=stream)
+        b.find(stream=stream)
+        return b.fetch()
+
+    tr, mem, toff = chain()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        tr, mem, toff = chain()
+    chain_s = (time.perf_counter() - t0) / steps
+    b.close()
+    fr.close()
+    return {"e2e": {"value": ws * V / e2e_s, "unit": "views/s", "h2d_bytes_per_step": int(V * view_bytes),
+                    "d2h_bytes_per_step": int(d2h)},
+            "pipeline": {"value": ws * V / chain_s, "unit": "views/s", "tracks_per_step": int(len(tr)),
+                         "what": "raw frames (device) -> grains -> batched track finding -> tracks to host, "
+                                 "wall clock per step"}}
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -442,11 +669,15 @@ def main():
     ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
     ap.add_argument("--served-rate", type=float, default=1000.0, help="Poisson rate of the served run (views/s)")
     ap.add_argument("--served-views", type=int, default=3000, help="views in the served run")
+    ap.add_argument("--frames-views", type=int, default=FRAMES_VIEWS,
+                    help="views per step of the frames workload (smaller for profiler captures)")
     ap.add_argument("--served-sweep", action="store_true",
                     help="only the served form: rates 100..5000 views/s over 10,000 views (seed 4)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "frames":
+        return run_frames_reference(args) if args.impl == "reference" else run_frames(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.served_sweep:
