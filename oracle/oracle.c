@@ -49,12 +49,20 @@ typedef __int128 i128;
 enum { OR_OK = 0, OR_ERR_INVALID_ARG = -1, OR_ERR_OUT_OF_RANGE = -2, OR_ERR_DUPLICATE = -3,
        OR_ERR_OOM = -6 };
 
+/* Variants (flags): OR_SINGLE_PASS -- every grain goes to the best candidate
+ * (candidate order) whose tube holds it, a candidate is a track iff at least
+ * min_hits grains went to it; OR_ANGLE_CUT -- a track is kept iff
+ * nhits >= cut_base + cut_slope * min(tan theta, cut_tan_max), theta the angle
+ * of its seed vector to the z axis (the grain-count cut of Section 3, Fig. 9c). */
+enum { OR_SINGLE_PASS = 1, OR_ANGLE_CUT = 2 };
+
 typedef struct {
     int32_t extent[3];
     int32_t seed_min, seed_max;
     int32_t tube_r;
     int32_t min_hits;
     uint32_t flags;
+    int32_t cut_base, cut_slope, cut_tan_max, reserved;
 } or_params;
 
 typedef struct {
@@ -114,7 +122,8 @@ or_ctx *or_create(const int32_t *xyz, int64_t n, const or_params *p, const int32
             *status = OR_ERR_INVALID_ARG; return NULL;
         }
     if (p->seed_min < 0 || p->seed_max < p->seed_min || p->tube_r < 0 || p->tube_r > (1 << 30) ||
-        p->min_hits < 1 || p->flags != 0) {
+        p->min_hits < 1 || (p->flags & ~(uint32_t)(OR_SINGLE_PASS | OR_ANGLE_CUT)) ||
+        ((p->flags & OR_ANGLE_CUT) && (p->cut_base < 0 || p->cut_slope < 0 || p->cut_tan_max < 0))) {
         *status = OR_ERR_INVALID_ARG; return NULL;
     }
     if (n > 2147483647LL) { *status = OR_ERR_INVALID_ARG; return NULL; }
@@ -519,6 +528,21 @@ void or_tracks_free(or_tracks *t) {
 /* The whole method.  Seeds and counts may optionally be returned (keep_seeds):
    then seed_lo/seed_hi/seed_count receive n_seeds entries ordered by (rank lo,
    rank hi) and must be freed with free(). */
+/* The grain-count cut (Section 3, Fig. 9c) as the plain inequality
+ * nhits >= cut_base + cut_slope * min(tan theta, cut_tan_max) with
+ * tan theta = sqrt(wx^2 + wy^2) / |wz| for the seed vector w = g_hi - g_lo,
+ * decided exactly: squares of non-negative sides compared in 128 bits. */
+static int angle_cut_keeps(const or_ctx *c, int32_t lo, int32_t hi, int64_t nhits) {
+    const int32_t *a = c->xyz + 3 * (int64_t)lo, *b = c->xyz + 3 * (int64_t)hi;
+    const i128 wx = b[0] - a[0], wy = b[1] - a[1], wz = b[2] - a[2];
+    const i128 t2 = wx * wx + wy * wy, z2 = wz * wz;        /* tan^2 theta = t2 / z2 */
+    const i128 need = (i128)nhits - c->p.cut_base;          /* must reach cut_slope * min(tan, tmax) */
+    if (need < 0) return 0;
+    const i128 tm = c->p.cut_tan_max, sl = c->p.cut_slope;
+    if (t2 >= tm * tm * z2) return need >= sl * tm;          /* tan theta >= tmax (or wz = 0) */
+    return need * need * z2 >= sl * sl * t2;                /* need >= sl * sqrt(t2 / z2) */
+}
+
 int or_find_tracks(const or_ctx *c, int nthreads, or_tracks *out, int keep_seeds, int32_t **seed_lo,
                    int32_t **seed_hi, int32_t **seed_count) {
     memset(out, 0, sizeof(*out));
@@ -562,13 +586,33 @@ int or_find_tracks(const or_ctx *c, int nthreads, or_tracks *out, int keep_seeds
     }
     out->moff[0] = 0;
     int64_t nt = 0, nm = 0;
+    /* single pass: first[g] = position (candidate order) of the first candidate
+     * whose tube holds grain g, or nc */
+    int64_t *first = NULL;
+    if (c->p.flags & OR_SINGLE_PASS) {
+        first = (int64_t *)malloc(sizeof(int64_t) * (size_t)(c->n > 0 ? c->n : 1));
+        if (!first) { free(s); free(used); free(buf); or_tracks_free(out); return OR_ERR_OOM; }
+        for (int64_t g = 0; g < c->n; ++g) first[g] = nc;
+        for (int64_t i = 0; i < nc; ++i) {
+            int64_t m = tube_scan(c, s[i].lo, s[i].hi, buf, c->n, NULL);
+            for (int64_t j = 0; j < m; ++j)
+                if (first[buf[j]] > i) first[buf[j]] = i;
+        }
+    }
     for (int64_t i = 0; i < nc; ++i) {
         int64_t m = tube_scan(c, s[i].lo, s[i].hi, buf, c->n, NULL);
         int64_t u = 0;
-        for (int64_t j = 0; j < m; ++j)
-            if (!used[buf[j]]) buf[u++] = buf[j];
-        if (u < c->p.min_hits) continue;
-        for (int64_t j = 0; j < u; ++j) used[buf[j]] = 1;
+        if (first) {   /* the grains that chose this candidate */
+            for (int64_t j = 0; j < m; ++j)
+                if (first[buf[j]] == i) buf[u++] = buf[j];
+            if (u < c->p.min_hits) continue;
+        } else {       /* sequential greedy: the grains no earlier track took */
+            for (int64_t j = 0; j < m; ++j)
+                if (!used[buf[j]]) buf[u++] = buf[j];
+            if (u < c->p.min_hits) continue;
+            for (int64_t j = 0; j < u; ++j) used[buf[j]] = 1;
+        }
+        if ((c->p.flags & OR_ANGLE_CUT) && !angle_cut_keeps(c, s[i].lo, s[i].hi, u)) continue;
         qsort(buf, (size_t)u, sizeof(int32_t), cmp_i32);
         if (nt + 1 >= tcap) {
             tcap *= 2;
@@ -582,13 +626,14 @@ int or_find_tracks(const or_ctx *c, int nthreads, or_tracks *out, int keep_seeds
             out->members = (int32_t *)realloc(out->members, sizeof(int32_t) * mcap);
         }
         if (!out->lo || !out->hi || !out->nhits || !out->moff || !out->members) {
-            free(s); free(used); free(buf); or_tracks_free(out); return OR_ERR_OOM;
+            free(s); free(used); free(buf); free(first); or_tracks_free(out); return OR_ERR_OOM;
         }
         out->lo[nt] = s[i].lo; out->hi[nt] = s[i].hi; out->nhits[nt] = (int32_t)u;
         memcpy(out->members + nm, buf, sizeof(int32_t) * (size_t)u);
         nm += u;
         out->moff[++nt] = nm;
     }
+    free(first);
     out->n_tracks = nt;
     free(s); free(used); free(buf);
     /* step 5: fit */

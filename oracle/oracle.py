@@ -39,9 +39,14 @@ class OracleError(RuntimeError):
         self.status = status
 
 
+SINGLE_PASS, ANGLE_CUT = 1, 2
+
+
 class _Params(C.Structure):
     _fields_ = [("extent", C.c_int32 * 3), ("seed_min", C.c_int32), ("seed_max", C.c_int32),
-                ("tube_r", C.c_int32), ("min_hits", C.c_int32), ("flags", C.c_uint32)]
+                ("tube_r", C.c_int32), ("min_hits", C.c_int32), ("flags", C.c_uint32),
+                ("cut_base", C.c_int32), ("cut_slope", C.c_int32), ("cut_tan_max", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class _Tracks(C.Structure):
@@ -117,12 +122,13 @@ def _pd(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_params(extent, seed_min, seed_max, tube_r, min_hits, flags=0):
+def make_params(extent, seed_min, seed_max, tube_r, min_hits, flags=0, cut=(0, 0, 0)):
     p = _Params()
     for k in range(3):
         p.extent[k] = int(extent[k])
     p.seed_min, p.seed_max, p.tube_r, p.min_hits, p.flags = (int(seed_min), int(seed_max),
                                                              int(tube_r), int(min_hits), int(flags))
+    p.cut_base, p.cut_slope, p.cut_tan_max = (int(c) for c in cut)
     return p
 
 
@@ -149,10 +155,11 @@ class Tracks:
 class Oracle:
     """One view prepared for the oracle: grains, canonical ranks, cell hash."""
 
-    def __init__(self, xyz, extent, seed_min, seed_max, tube_r, min_hits, flags=0, cell=PAPER_CELL):
+    def __init__(self, xyz, extent, seed_min, seed_max, tube_r, min_hits, flags=0, cell=PAPER_CELL,
+                 cut=(0, 0, 0)):
         L = lib()
         self.xyz = np.ascontiguousarray(np.asarray(xyz, dtype=np.int32).reshape(-1, 3))
-        self.params = make_params(extent, seed_min, seed_max, tube_r, min_hits, flags)
+        self.params = make_params(extent, seed_min, seed_max, tube_r, min_hits, flags, cut)
         cell_arr = np.ascontiguousarray(np.asarray(cell, dtype=np.int32))
         st = np.zeros(1, dtype=np.int32)
         self._h = L.or_create(_p32(self.xyz), self.xyz.shape[0], C.byref(self.params), _p32(cell_arr),
