@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define ET_ABI_VERSION 1
+#define ET_ABI_VERSION 2
 
 typedef int32_t et_status;
 #define ET_OK                    0
@@ -66,19 +66,44 @@ typedef int32_t et_status;
 #define ET_ERR_CUDA             -9  /* a CUDA runtime call failed */
 #define ET_ERR_NOT_READY       -10  /* nothing has been computed yet */
 
+/* Variants (et_params.flags).  The default (0) is the sequential greedy
+ * association described at the top of this file.
+ *
+ * ET_FLAG_SINGLE_PASS -- the other reading of "each grain is exclusively
+ *   associated with one track" (Section 2): every grain of a candidate's tube
+ *   goes to the best candidate (candidate order above) whose tube holds it, in
+ *   one pass; a candidate becomes a track iff at least min_hits grains went to
+ *   it, and owns exactly those.  A grain whose best candidate is rejected stays
+ *   unassigned.
+ * ET_FLAG_ANGLE_CUT -- the grain-count cut against background of Section 3
+ *   (Fig. 9c: larger-angle tracks have more grains): a track is kept iff
+ *       nhits >= cut_base + cut_slope * min(tan theta, cut_tan_max),
+ *   theta being the angle of its seed vector w = g_hi - g_lo to the z axis
+ *   (tan theta = sqrt(w_x^2 + w_y^2) / |w_z|, infinite for w_z = 0), decided
+ *   in exact integer arithmetic.  Dropped tracks keep their grains (the cut
+ *   selects tracks; it does not re-associate grains). */
+#define ET_FLAG_SINGLE_PASS 1u
+#define ET_FLAG_ANGLE_CUT   2u
+
 /* Tracking parameters (Section 2).  Distances in coordinate units.
  * extent[k] > 0: grains must lie in [0, extent[k]).  Limits enforced:
  *   extent[k] <= 2^21, views of at most 2^21 - 1 grains,
  *   0 <= seed_min <= seed_max, 1 <= seed_max, 0 <= tube_r <= 2^20, 1 <= min_hits,
  *   (extent[a] + extent[b]) * seed_max < 2^31 for every pair of axes a != b
  *   (so every cross-product component is an exact int32), else
- *   ET_ERR_PRECONDITION.  flags must be 0 (reserved for variants). */
+ *   ET_ERR_PRECONDITION.  flags: a combination of the ET_FLAG_* bits above.
+ *   With ET_FLAG_ANGLE_CUT: 0 <= cut_base <= 2^21, 0 <= cut_slope <= 2^20,
+ *   0 <= cut_tan_max <= 1024 (cut fields are ignored without it); reserved = 0. */
 typedef struct {
     int32_t extent[3];
     int32_t seed_min, seed_max;
     int32_t tube_r;
     int32_t min_hits;
     uint32_t flags;
+    int32_t cut_base;       /* grains */
+    int32_t cut_slope;      /* grains per unit of tan theta */
+    int32_t cut_tan_max;    /* tan theta above this counts as this */
+    int32_t reserved;
 } et_params;
 
 /* Optional tuning.  Zero fields mean "choose automatically".  Results never

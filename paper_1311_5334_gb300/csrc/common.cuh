@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "et.h"   // ET_FLAG_* variant bits
+
 namespace et {
 
 typedef unsigned long long u64;
@@ -56,6 +58,8 @@ struct Batch {
     int ext[3];
     int smin, smax, r, H;
     long long smin2, smax2, r2;
+    unsigned flags;          // ET_FLAG_* variants
+    int cut_base, cut_slope, cut_tmax;   // angle cut (ET_FLAG_ANGLE_CUT)
     // cell grid (identical for all views)
     int cs[3];           // cell edge per axis
     int nc[3];           // cells per axis
@@ -164,6 +168,7 @@ void launch_seed_fill(const Batch &b, const Work &w, cudaStream_t st);
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st);
 void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st);
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st);
+void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st);
 
 // merge.cu
 int merge_grid_blocks(int device);

@@ -242,6 +242,61 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     }
 }
 
+// Angle cut (ET_FLAG_ANGLE_CUT): keep a track iff
+//     nhits >= cut_base + cut_slope * min(tan theta, cut_tmax),
+// tan theta = sqrt(wx^2 + wy^2) / |wz| for the seed vector w, in exact
+// integers: with A = nhits - cut_base, keep iff A >= 0 and either
+// wx^2 + wy^2 >= cut_tmax^2 wz^2 (tan theta capped) and A >= cut_slope cut_tmax,
+// or A^2 wz^2 >= cut_slope^2 (wx^2 + wy^2) (128-bit products).
+__device__ __forceinline__ bool angle_cut_keeps(const Batch &b, int4 glo, int4 ghi, long long nhits) {
+    const long long A = nhits - b.cut_base;
+    if (A < 0) return false;
+    const long long wx = ghi.x - glo.x, wy = ghi.y - glo.y, wz = ghi.z - glo.z;
+    const unsigned long long t2 = (unsigned long long)(wx * wx + wy * wy), z2 = (unsigned long long)(wz * wz);
+    const unsigned long long tm = (unsigned long long)b.cut_tmax, sl = (unsigned long long)b.cut_slope;
+    if ((unsigned __int128)t2 >= (unsigned __int128)(tm * tm) * z2) return (unsigned long long)A >= sl * tm;
+    return (unsigned __int128)((unsigned long long)A * (unsigned long long)A) * z2 >=
+           (unsigned __int128)(sl * sl) * t2;
+}
+
+// Single-pass association (ET_FLAG_SINGLE_PASS), step 1: every grain keeps the
+// smallest key of the candidates whose tube holds it (one warp per candidate).
+__global__ void k_sp_best(Batch b, Work w) {
+    if (input_failed(b.ctl)) return;
+    const u64 nc = min(b.ctl->n_cand, w.cand_cap);
+    const int lane = threadIdx.x & 31;
+    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5);
+    for (u64 c = (u64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nc; c += nw) {
+        const u64 key = w.c_key[c], m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
+        for (u64 m = m0 + lane; m < m1; m += 32) atomicMin(&w.best[0][w.members[m]], key);
+    }
+}
+
+// Step 2: a candidate owns the grains whose smallest key is its own; it is a
+// track iff it owns at least min_hits of them.
+__global__ void k_sp_own(Batch b, Work w) {
+    if (input_failed(b.ctl)) return;
+    const u64 nc = min(b.ctl->n_cand, w.cand_cap);
+    const int lane = threadIdx.x & 31;
+    const u64 nw = (u64)gridDim.x * (blockDim.x >> 5);
+    for (u64 c = (u64)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nc; c += nw) {
+        const u64 key = w.c_key[c], m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
+        u32 own = 0;
+        for (u64 m = m0 + lane; m < m1; m += 32) own += w.best[0][w.members[m]] == key;
+        own = __reduce_add_sync(0xffffffffu, own);
+        const bool accept = own >= (u32)b.H;
+        if (accept)
+            for (u64 m = m0 + lane; m < m1; m += 32) {
+                const int g = w.members[m];
+                if (w.best[0][g] == key) w.owner[g] = (int)c;
+            }
+        if (lane == 0) {
+            w.c_nfree[c] = own;
+            w.c_state[c] = accept ? CS_ACCEPTED : CS_REJECTED;
+        }
+    }
+}
+
 // Accepted candidates -> list (any order) with sort keys.
 __global__ void k_collect(Batch b, Work w, Out o) {
     if (input_failed(b.ctl)) return;
@@ -249,6 +304,8 @@ __global__ void k_collect(Batch b, Work w, Out o) {
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
         if (w.c_state[c] != CS_ACCEPTED) continue;
+        if ((b.flags & ET_FLAG_ANGLE_CUT) && !angle_cut_keeps(b, b.gr[w.c_lo[c]], b.gr[w.c_hi[c]], w.c_nfree[c]))
+            continue;
         const u64 i = atomicAdd(&b.ctl->n_acc, 1ull);
         o.sort_k[0][i] = w.c_key[c];
         o.sort_v[0][i] = (u32)c;
@@ -469,6 +526,12 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
     Work ww = w;
     void *args[] = {&bb, &ww};
     return cudaLaunchCooperativeKernel((const void *)k_merge, dim3(grid), dim3(MT), args, 0, st);
+}
+
+void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st) {
+    const unsigned g = sm_count() * 8;
+    k_sp_best<<<g, 256, 0, st>>>(b, w);
+    k_sp_own<<<g, 256, 0, st>>>(b, w);
 }
 
 // Accepted list sorted by (view, key); per-view track offsets; member offsets;

@@ -91,7 +91,15 @@ et_status check_params(const et_params *p) {
         return fail(ET_ERR_INVALID_ARG, "seed window [%d, %d) invalid", p->seed_min, p->seed_max);
     if (p->tube_r < 0 || p->tube_r > (1 << 20)) return fail(ET_ERR_INVALID_ARG, "tube_r = %d", p->tube_r);
     if (p->min_hits < 1) return fail(ET_ERR_INVALID_ARG, "min_hits = %d < 1", p->min_hits);
-    if (p->flags != 0) return fail(ET_ERR_INVALID_ARG, "flags = %u: no variant is defined", p->flags);
+    if (p->flags & ~(ET_FLAG_SINGLE_PASS | ET_FLAG_ANGLE_CUT))
+        return fail(ET_ERR_INVALID_ARG, "flags = %u: unknown variant bits", p->flags);
+    if (p->flags & ET_FLAG_ANGLE_CUT) {
+        if (p->cut_base < 0 || p->cut_base > (1 << 21) || p->cut_slope < 0 || p->cut_slope > (1 << 20) ||
+            p->cut_tan_max < 0 || p->cut_tan_max > 1024)
+            return fail(ET_ERR_INVALID_ARG, "angle cut (%d, %d, %d) outside the limits", p->cut_base,
+                        p->cut_slope, p->cut_tan_max);
+    }
+    if (p->reserved != 0) return fail(ET_ERR_INVALID_ARG, "reserved field must be 0");
     for (int a = 0; a < 3; ++a)
         for (int c = a + 1; c < 3; ++c) {
             long long v = ((long long)p->extent[a] + p->extent[c]) * (long long)p->seed_max;
@@ -436,6 +444,11 @@ Batch BatchRT::dev_batch() const {
     b.smin2 = (long long)p.seed_min * p.seed_min;
     b.smax2 = (long long)p.seed_max * p.seed_max;
     b.r2 = (long long)p.tube_r * p.tube_r;
+    b.flags = p.flags;
+    const bool cut = (p.flags & ET_FLAG_ANGLE_CUT) != 0;
+    b.cut_base = cut ? p.cut_base : 0;
+    b.cut_slope = cut ? p.cut_slope : 0;
+    b.cut_tmax = cut ? p.cut_tan_max : 0;
     b.ncell = (int)ncell;
     for (int k = 0; k < 3; ++k) {
         b.csy[k] = csy[k];
@@ -543,8 +556,12 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         cudaMemsetAsync(best[1], 0xFF, sizeof(u64) * n, st);
         cudaMemsetAsync(owner, 0xFF, sizeof(int) * n, st);
         mark(4, st);
-        cudaError_t e = launch_merge_coop(b, w, ctx->merge_grid, st);
-        if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        if (p.flags & ET_FLAG_SINGLE_PASS) {
+            launch_single_pass(b, w, st);
+        } else {
+            cudaError_t e = launch_merge_coop(b, w, ctx->merge_grid, st);
+            if (e != cudaSuccess) return cuda_fail(e, "merge launch");
+        }
         mark(5, st);
         launch_output(b, w, o, (long long)cap_cand, std::max<long long>(n, 1), temp, st);
         mark(6, st);

@@ -38,9 +38,14 @@ class EtError(RuntimeError):
         self.status = status
 
 
+FLAG_SINGLE_PASS, FLAG_ANGLE_CUT = 1, 2
+
+
 class Params(C.Structure):
     _fields_ = [("extent", C.c_int32 * 3), ("seed_min", C.c_int32), ("seed_max", C.c_int32),
-                ("tube_r", C.c_int32), ("min_hits", C.c_int32), ("flags", C.c_uint32)]
+                ("tube_r", C.c_int32), ("min_hits", C.c_int32), ("flags", C.c_uint32),
+                ("cut_base", C.c_int32), ("cut_slope", C.c_int32), ("cut_tan_max", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Tuning(C.Structure):
@@ -78,7 +83,8 @@ class FrameParams(C.Structure):
 
 class FramesStats(C.Structure):
     _fields_ = [("n_views", C.c_int64), ("n_voxels", C.c_int64), ("n_candidates", C.c_int64),
-                ("n_grains", C.c_int64), ("kernel_ms", C.c_float), ("run_ms", C.c_float)]
+                ("n_grains", C.c_int64), ("kernel_ms", C.c_float), ("run_ms", C.c_float),
+                ("kernel_launches", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -172,12 +178,13 @@ def _check(status):
     return status
 
 
-def make_params(extent, seed_min, seed_max, tube_r, min_hits, flags=0) -> Params:
+def make_params(extent, seed_min, seed_max, tube_r, min_hits, flags=0, cut=(0, 0, 0)) -> Params:
     p = Params()
     for k in range(3):
         p.extent[k] = int(extent[k])
     p.seed_min, p.seed_max, p.tube_r, p.min_hits, p.flags = (int(seed_min), int(seed_max), int(tube_r),
                                                              int(min_hits), int(flags))
+    p.cut_base, p.cut_slope, p.cut_tan_max = (int(c) for c in cut)
     return p
 
 
@@ -185,7 +192,7 @@ def _params(pp) -> Params:
     if isinstance(pp, Params):
         return pp
     return make_params(pp["extent"], pp["seed_min"], pp["seed_max"], pp["tube_r"], pp["min_hits"],
-                       pp.get("flags", 0))
+                       pp.get("flags", 0), pp.get("cut", (0, 0, 0)))
 
 
 def _host_grains(xyz):

@@ -52,9 +52,11 @@ class View:
         return int(self.xyz.shape[0])
 
 
-def params(extent, seed_min=SEED_MIN, seed_max=SEED_MAX, tube_r=TUBE_R, min_hits=MIN_HITS):
+def params(extent, seed_min=SEED_MIN, seed_max=SEED_MAX, tube_r=TUBE_R, min_hits=MIN_HITS, flags=0,
+           cut=(0, 0, 0)):
     return dict(extent=tuple(int(e) for e in extent), seed_min=int(seed_min),
-                seed_max=int(seed_max), tube_r=int(tube_r), min_hits=int(min_hits))
+                seed_max=int(seed_max), tube_r=int(tube_r), min_hits=int(min_hits), flags=int(flags),
+                cut=tuple(int(c) for c in cut))
 
 
 def _isotropic(rng, k):
@@ -245,7 +247,7 @@ class Frames:
 
 
 def render(px, py, pz, amp, shape, seed, row_pitch=None, psf_xy=1.0, psf_z=0.8, dark=55.0,
-           noise=3.0, col_sigma=0.08, px_sigma=0.03, margin=10, quantum=None):
+           noise=3.0, col_sigma=0.08, px_sigma=0.03, margin=10, quantum=None, camera_seed=None):
     """Raw frames of grains at voxel positions (px, py, pz) with pulse heights amp.
 
     Each grain is a Gaussian blob (sigma psf_xy pixels, psf_z frames).  A pixel
@@ -255,13 +257,15 @@ def render(px, py, pz, amp, shape, seed, row_pitch=None, psf_xy=1.0, psf_z=0.8, 
     multiples of it first (many equal neighbours).  The calibration returned
     with the frames: gain = 128 / s and a threshold at the pixel's corrected
     background plus margin.  Rows are row_pitch >= W bytes; the padding holds
-    random bytes.
+    random bytes.  camera_seed (default: seed) draws the sensitivity pattern,
+    so views rendered with one camera_seed share one calibration.
     """
     D, H, W = shape
     row_pitch = W if row_pitch is None else int(row_pitch)
     rng = np.random.default_rng(seed)
-    col = np.clip(rng.standard_normal(W), -2.5, 2.5)
-    s = 1.0 + col_sigma * col[None, :] + px_sigma * np.clip(rng.standard_normal((H, W)), -3.0, 3.0)
+    cam = np.random.default_rng(seed if camera_seed is None else camera_seed)
+    col = np.clip(cam.standard_normal(W), -2.5, 2.5)
+    s = 1.0 + col_sigma * col[None, :] + px_sigma * np.clip(cam.standard_normal((H, W)), -3.0, 3.0)
     gain = np.clip(np.rint(128.0 / s), 0, 255).astype(np.uint8)
     thr = np.clip(np.rint(dark * s * gain / 128.0) + margin, 0, 255).astype(np.uint8)
 
@@ -291,7 +295,8 @@ def render(px, py, pz, amp, shape, seed, row_pitch=None, psf_xy=1.0, psf_z=0.8, 
     return Frames(raw=raw, gain=gain, thr=thr, width=W)
 
 
-def frames_view(seed, n_fog=10000, n_through=100, n_short=0, row_pitch=None, amp=(60.0, 110.0)):
+def frames_view(seed, n_fog=10000, n_through=100, n_short=0, row_pitch=None, amp=(60.0, 110.0),
+                camera_seed=None):
     """One full 1280 x 1024 x 40 view: the grains of make_view on the camera's
     300 x 250 x 50 um volume, rendered into raw frames.  Returns (View, Frames)."""
     v = make_view(seed, extent=FRAME_EXTENT, n_fog=n_fog, n_through=n_through, n_short=n_short)
@@ -301,7 +306,8 @@ def frames_view(seed, n_fog=10000, n_through=100, n_short=0, row_pitch=None, amp
     py = xyz[:, 1] * PITCH_DEN[1] / PITCH_NUM[1]
     pz = xyz[:, 2] * PITCH_DEN[2] / PITCH_NUM[2]
     a = rng.uniform(amp[0], amp[1], v.n)
-    fr = render(px, py, pz, a, (FRAME_D, FRAME_H, FRAME_W), seed=[seed, 8], row_pitch=row_pitch)
+    fr = render(px, py, pz, a, (FRAME_D, FRAME_H, FRAME_W), seed=[seed, 8], row_pitch=row_pitch,
+                camera_seed=camera_seed)
     return v, fr
 
 
