@@ -162,18 +162,26 @@ def make_workload(name="batched"):
     return views, xyz, offs
 
 
-def oracle_views_per_s(views, budget_s, start=0):
+def workload_params(views, args=None):
+    """Tracking parameters of the workload, with the variant flags of the command line."""
+    if args is None:
+        return synth.params(views[0].extent)
+    return synth.params(views[0].extent, flags=args.flags, cut=tuple(int(c) for c in args.cut.split(",")))
+
+
+def oracle_views_per_s(views, budget_s, start=0, args=None):
     """Times the oracle on views[start:] until budget_s of wall time is used."""
     from oracle import oracle as O
     O.build()
-    p = synth.params(views[0].extent)
+    p = workload_params(views, args)
     done, seeds, t_used = 0, 0, 0.0
     k = start
     names = []
     while t_used < budget_s and done < len(views):
         v = views[k % len(views)]
         t0 = time.perf_counter()
-        with O.Oracle(v.xyz, v.extent, p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"]) as o:
+        with O.Oracle(v.xyz, v.extent, p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"],
+                      flags=p["flags"], cut=p["cut"]) as o:
             tr = o.find_tracks()
         t_used += time.perf_counter() - t0
         done += 1
@@ -194,11 +202,11 @@ def run_reference(args):
     per_step = max(1.0, float(os.environ.get("ET_REF_STEP_S", "4")))
     k = 0
     for _ in range(args.warmup):
-        d, _, _, _ = oracle_views_per_s(views, per_step / 4, start=k)
+        d, _, _, _ = oracle_views_per_s(views, per_step / 4, start=k, args=args)
         k += d
     tot_v, tot_s, tot_t = 0, 0, 0.0
     for _ in range(args.steps):
-        d, s, t, _ = oracle_views_per_s(views, per_step, start=k)
+        d, s, t, _ = oracle_views_per_s(views, per_step, start=k, args=args)
         k += d
         tot_v += d
         tot_s += s
@@ -238,7 +246,7 @@ def run_ours(args):
 
     views, xyz_h, offs = make_workload(args.workload)
     n_views = len(views)
-    params = synth.params(views[0].extent)
+    params = workload_params(views, args)
     # a dedicated stream: the legacy default stream (handle 0) would mean
     # "the context's own stream" to the library
     stream = torch.cuda.Stream()
@@ -318,6 +326,7 @@ def run_ours(args):
                        "candidate_members_per_step": ref_stats["n_members"],
                        "merge_rounds": ref_stats["merge_rounds"], "cell_units": list(ref_stats["cell"]),
                        "autotune": tuned,
+                       "variant": {"flags": params["flags"], "cut": list(params["cut"])},
                        "l2": "flushed between timed steps (256 MiB write); inputs resident in HBM",
                        "parallelism": f"replicas: one {n_views}-view batch per rank x {ws}"},
             "seeds_per_s": seeds_per_s,
@@ -342,7 +351,7 @@ def run_ours(args):
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra:
         budget = float(os.environ.get("ET_CPU_BASELINE_S", "15"))
-        d, s, t, names = oracle_views_per_s(views, budget)
+        d, s, t, names = oracle_views_per_s(views, budget, args=args)
         line["cpu_baseline"] = {"value": d / t, "unit": "views/s", "cores": os.cpu_count(), "kind": "oracle",
                                 "sample": f"views {names[0]}..{names[-1]} ({d} of {n_views}) of the step, "
                                           f"{t:.1f} s; counting parallel over all cores (OpenMP), "
@@ -669,6 +678,9 @@ def main():
     ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
     ap.add_argument("--served-rate", type=float, default=1000.0, help="Poisson rate of the served run (views/s)")
     ap.add_argument("--served-views", type=int, default=3000, help="views in the served run")
+    ap.add_argument("--flags", type=int, default=0,
+                    help="et_params.flags: 1 single-pass association, 2 angle cut (tracking workloads)")
+    ap.add_argument("--cut", default="0,0,0", help="angle cut base,slope,tan_max (with --flags 2)")
     ap.add_argument("--frames-views", type=int, default=FRAMES_VIEWS,
                     help="views per step of the frames workload (smaller for profiler captures)")
     ap.add_argument("--served-sweep", action="store_true",

@@ -46,6 +46,7 @@ class View:
     label: np.ndarray        # (N,) int32: track index, or -1 for fog
     extent: tuple            # (Ex, Ey, Ez) in units; coordinates lie in [0, E)
     n_tracks: int
+    truth: np.ndarray = None   # (n_tracks, 6): a point (um) and the unit direction of each track's line
 
     @property
     def n(self) -> int:
@@ -125,18 +126,21 @@ def make_view(seed, extent=(300 * UM, 300 * UM, 50 * UM), n_fog=2000, n_through=
     labels.append(np.full(n_fog, -1, dtype=np.int32))
 
     track_raw = []  # per track: (points in um) for re-jitter on duplicates
+    truth = []      # per track: point and direction of its line (um)
     dirs = _isotropic(rng, n_through + n_short)
     for k in range(n_through):
         p = rng.uniform(0.0, 1.0, 3) * e_um
         d = dirs[k]
         t0, t1 = _chord(p, d, e_um)
         track_raw.append(_track_points(rng, p, d, t0, t1, gap_through_um, False))
+        truth.append(np.concatenate([p, d]))
     for k in range(n_short):
         p = rng.uniform(0.0, 1.0, 3) * e_um
         d = dirs[n_through + k]
         rng_um = rng.uniform(*short_range_um)
         _, t1 = _chord(p, d, e_um)
         track_raw.append(_track_points(rng, p, d, 0.0, min(rng_um, t1), gap_short_um, True))
+        truth.append(np.concatenate([p, d]))
 
     for k, pts in enumerate(track_raw):
         pieces.append(_to_units(rng, pts, extent, jitter_xy_um, jitter_z_um))
@@ -166,7 +170,7 @@ def make_view(seed, extent=(300 * UM, 300 * UM, 50 * UM), n_fog=2000, n_through=
     perm = rng.permutation(xyz.shape[0])
     return View(xyz=np.ascontiguousarray(xyz[perm].astype(np.int32)),
                 label=np.ascontiguousarray(label[perm]), extent=extent,
-                n_tracks=n_through + n_short)
+                n_tracks=n_through + n_short, truth=np.array(truth, dtype=np.float64).reshape(-1, 6))
 
 
 # ---------------------------------------------------------------- workloads
