@@ -265,7 +265,7 @@ def run_ours(args):
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
         tuned = {"cell": list(cell), "row_lists": batch.tuning["row_lists"], "ms_per_run": ms,
-                 "how": "et_batch_autotune: fastest of 8 cell shapes with x rows, then the best 2 with x+y rows"}
+                 "how": "et_batch_autotune: fastest of 8 cell shapes, each with x rows and with x+y rows"}
 
     def step():
         batch.load(xyz_d, offs, stream=stream)

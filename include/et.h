@@ -231,8 +231,8 @@ et_status et_batch_load(et_batch *b, const int32_t *xyz, const int64_t *offsets,
 et_status et_batch_set_tuning(et_batch *b, const et_tuning *tuning);
 /* Picks the cell-list shape for the loaded batch by timing the whole path on
  * it: up to max_trials candidate shapes derived from the batch's mean grain
- * density (cubic and anisotropic, rows along x kept short) with one cell list,
- * then the two best shapes with both lists, two runs each, CUDA-event timed;
+ * density (mostly anisotropic, cells along the x rows kept short), each with
+ * one cell list and with both lists, two runs each, CUDA-event timed;
  * the fastest is kept as the batch's tuning and returned in *chosen (may be
  * NULL), its time per run in *best_ms (may be NULL).
  * Synchronous.  Results never depend on the choice, only the speed does. */

@@ -163,8 +163,8 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
     const double nmean = V > 0 ? std::max(1.0, (double)N / V) : 1.0;
     const double s0 = std::cbrt(0.35 * vol / nmean);
     // (x, y, z) factors of s0; rows run along x, so x cells may be short
-    static const double cand[][3] = {{1.0, 1.0, 1.0}, {1.3, 1.3, 1.3}, {0.33, 1.3, 1.3}, {0.33, 1.6, 1.6},
-                                     {0.8, 0.8, 0.8}, {0.5, 1.6, 1.3}, {0.33, 2.0, 2.0}, {1.6, 1.6, 1.6}};
+    static const double cand[][3] = {{0.22, 1.1, 1.1}, {0.33, 1.3, 1.3}, {0.16, 1.1, 1.1}, {0.27, 0.95, 0.95},
+                                     {0.22, 1.3, 1.3}, {0.33, 1.1, 1.1}, {0.5, 1.6, 1.3}, {1.0, 1.0, 1.0}};
     const int ncand = (int)(sizeof cand / sizeof cand[0]);
     if (max_trials <= 0 || max_trials > ncand) max_trials = ncand;
     const et_tuning saved = tune;
@@ -172,23 +172,11 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
     profile = true;
     float best = 3.0e38f;
     et_tuning best_t = tune;
-    std::vector<std::pair<float, et_tuning>> tried;
-    for (int k = 0; k < max_trials + 2; ++k) {
+    for (int k = 0; k < 2 * max_trials; ++k) {   // every shape with one and with both cell lists
         et_tuning t = saved;
-        if (k < max_trials) {
-            for (int a = 0; a < 3; ++a)
-                t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k][a])));
-            t.row_lists = 1;
-        } else {   // the two fastest shapes again, with the second (y-row) list
-            std::sort(tried.begin(), tried.end(),
-                      [](const std::pair<float, et_tuning> &x, const std::pair<float, et_tuning> &y) {
-                          return x.first < y.first;
-                      });
-            const size_t i = (size_t)(k - max_trials);
-            if (i >= tried.size()) break;
-            t = tried[i].second;
-            t.row_lists = 2;
-        }
+        for (int a = 0; a < 3; ++a)
+            t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k / 2][a])));
+        t.row_lists = 1 + (k & 1);
         tune = t;
         choose_cells();
         if ((double)V * (double)std::max(ncell, ncelly) >= 4.0e9) continue;
@@ -219,7 +207,6 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
             float ms = 0;
             if (cudaEventElapsedTime(&ms, ev[0], ev[NSTAGE]) == cudaSuccess) t_best = std::min(t_best, ms);
         }
-        if (k < max_trials) tried.push_back({t_best, t});
         if (t_best < best) {
             best = t_best;
             best_t = t;
@@ -383,6 +370,31 @@ unsigned long long BatchRT::layout_generation() const {
     for (const Group *x : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
         g = g * 1315423911ull + x->generation;
     return g;
+}
+
+// Everything a captured launch sequence bakes into its kernel arguments and
+// launch shapes: buffer layouts, batch shape, cell grids, capacities.  A
+// captured graph is replayed only while this is unchanged.
+unsigned long long BatchRT::graph_signature() const {
+    unsigned long long h = layout_generation();
+    auto mix = [&h](unsigned long long v) { h = (h ^ v) * 0x100000001b3ull + 0x9e3779b97f4a7c15ull; };
+    mix((unsigned long long)N);
+    mix((unsigned long long)V);
+    mix((unsigned long long)maxN);
+    for (int k = 0; k < 3; ++k) {
+        mix((unsigned long long)cs[k]);
+        mix((unsigned long long)nc[k]);
+        mix((unsigned long long)csy[k]);
+        mix((unsigned long long)ncy[k]);
+    }
+    mix((unsigned long long)ncell);
+    mix((unsigned long long)ncelly);
+    mix(dual ? 1ull : 0ull);
+    mix(cap_seeds);
+    mix(cap_cand);
+    mix(cap_members);
+    mix(cap_rec);
+    return h;
 }
 
 et_status BatchRT::load(const int32_t *xyz, const int64_t *offsets, int nv, bool on_device, cudaStream_t st) {
@@ -578,8 +590,7 @@ et_status BatchRT::find(cudaStream_t st, bool use_graph) {
     if (!st) st = ctx->stream;
     et_status s;
     if (use_graph && N > 0) {
-        const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V ^
-                                       (profile ? 0x8000000000000000ull : 0ull);
+        const unsigned long long key = graph_signature() ^ (profile ? 0x8000000000000000ull : 0ull);
         if (!gexec || key != graph_key) {
             if (gexec) {
                 cudaGraphExecDestroy(gexec);
@@ -711,7 +722,7 @@ void BatchRT::mark(int stage, cudaStream_t st) {
 // Number of kernels in one run of the path: capture the launch sequence into
 // a graph that is never executed and count its kernel nodes.
 int BatchRT::count_kernels() {
-    const unsigned long long key = layout_generation() ^ ((unsigned long long)N << 20) ^ (unsigned long long)V;
+    const unsigned long long key = graph_signature();
     if (kernel_launches >= 0 && key == launches_key) return kernel_launches;
     if (!loaded || N == 0) return 0;
     cudaStream_t st = nullptr;

@@ -115,6 +115,7 @@ struct BatchRT {
     void estimate_caps();
     et_status reserve();
     unsigned long long layout_generation() const;
+    unsigned long long graph_signature() const;
     et_status load(const int32_t *xyz, const int64_t *offsets, int nv, bool on_device, cudaStream_t st);
     Batch dev_batch() const;
     Work dev_work() const;

@@ -207,6 +207,32 @@ def test_batched_matches_oracle_per_view(et, ctx, oracle_mod):
         b.close()
 
 
+def test_graph_replay_follows_tuning_changes(et, ctx, oracle_mod):
+    # a captured launch sequence must not outlive the cell grid it was captured for
+    views = [v for v in synth.batched(n_views=12, seed=3) if v.n < 20000][:6]
+    xyz, offs = synth.concat(views)
+    p = synth.params(views[0].extent)
+    want = [oracle_run(oracle_mod, v.xyz, p).as_tuples() for v in views]
+    b = et.Batch(ctx, p)
+    try:
+        seen = set()
+        for cell, rows in [((300, 300, 300), 1), ((152, 598, 598), 2), ((500, 200, 400), 1), ((300, 300, 300), 1)]:
+            b.set_tuning(cell, row_lists=rows)
+            b.load(xyz, offs)
+            b.find(use_graph=False)
+            b.sync()
+            direct = b.stats()["n_tests"]   # tube tests depend on the cell grid
+            b.find(use_graph=True)
+            tracks, members, voff = b.fetch()
+            assert b.stats()["n_tests"] == direct
+            seen.add(direct)
+            for k in range(len(views)):
+                assert et.track_tuples(tracks[voff[k]:voff[k + 1]], members) == want[k]
+        assert len(seen) == 3   # three different grids, three different test counts
+    finally:
+        b.close()
+
+
 # ------------------------------------------------------------------ edge cases
 
 def _p(extent=(1000, 1000, 1000), smin=10, smax=300, r=5, h=3):
