@@ -58,8 +58,10 @@ typedef struct {
     int64_t n_voxels;        /* voxels examined: n_views * depth * height * width */
     int64_t n_candidates;    /* voxels with f > grain_threshold */
     int64_t n_grains;
-    float kernel_ms;         /* CUDA-event time of the recognition kernel (0 if not measured) */
-    float run_ms;            /* CUDA-event time of the whole run on the device */
+    float kernel_ms;         /* CUDA-event time of the recognition kernel */
+    float run_ms;            /* CUDA-event time of the whole run on the device (upload included) */
+    int32_t kernel_launches; /* kernels one run launches (recognition, sort passes, gather, scan) */
+    int32_t reserved;
 } et_frames_stats;
 
 typedef struct et_frames et_frames;
