@@ -71,6 +71,7 @@ struct Batch {
     const int *xyz_in;   // N x 3 input, caller order
     int4 *gr;            // canonical order: x, y, z, caller index within the view
     int4 *gc;            // cell order: x, y, z, canonical (global) index
+    u64 *gp;             // cell order: x | y << 21 | z << 42 (the tube counts' 8-byte grain loads)
     u32 *cell_start;     // V * ncell + 1
     // second cell list with rows along y: cell edges (cs[1], cs[0], cs[2]),
     // index cy + ncy[1] * (cx + ncy[0] * cz); lines whose |w_y| > |w_x| walk it
@@ -79,6 +80,7 @@ struct Batch {
     float icsy[3];
     int ncelly;
     int4 *gcy;
+    u64 *gpy;
     u32 *cell_start_y;   // V * ncelly + 1
     Ctl *ctl;
 };
@@ -128,6 +130,14 @@ __device__ __forceinline__ int view_of(const long long *goff, int V, long long g
         if (goff[mid] <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Coordinates (each below 2^21) packed into 8 bytes and back.
+__device__ __forceinline__ u64 pack_xyz(int x, int y, int z) {
+    return (u64)(unsigned)x | ((u64)(unsigned)y << 21) | ((u64)(unsigned)z << 42);
+}
+__device__ __forceinline__ int4 unpack_xyz(u64 p) {
+    return make_int4((int)(p & 0x1fffffu), (int)((p >> 21) & 0x1fffffu), (int)(p >> 42), 0);
 }
 
 __device__ __forceinline__ bool input_failed(const Ctl *ctl) {

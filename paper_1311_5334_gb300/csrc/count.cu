@@ -245,7 +245,15 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
 // in this pass (an OR-reduction of one-hot start bits and a popcount) and reads
 // the range from a per-warp table (tbl) indexed by that rank.  So every pass
 // tests 32 grains, however unevenly the rows of the round hold them.
-template <class Hit>
+// Grain k of the x-row (list 0) or y-row (list 1) cell order: 8-byte packed
+// coordinates (PACKED, w = 0) or the 16-byte record with the canonical index.
+template <bool PACKED>
+__device__ __forceinline__ int4 grain_at(const Batch &b, int list, u32 k) {
+    if (PACKED) return unpack_xyz((list ? b.gpy : b.gp)[k]);
+    return (list ? b.gcy : b.gc)[k];
+}
+
+template <bool PACKED, class Hit>
 __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u32 &tests,
                                            Hit &&hit) {
     const int lane = threadIdx.x & 31;
@@ -332,14 +340,13 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                         b1 = beg;
                         n1 = end - beg;
                     } else {   // rare: a third row, tested by this lane alone
-                        const int4 *__restrict__ gl = list ? b.gcy : b.gc;
                         const int4 e0 = sp.i4(0, own), e1 = sp.i4(1, own);
                         const int3 a = make_int3(e0.x, e0.y, e0.z), d = make_int3(e0.w, e1.x, e1.y);
                         const long long R =
                             (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
                         tests += end - beg;
                         for (u32 k = beg; k < end; ++k) {
-                            const int4 g = gl[k];
+                            const int4 g = grain_at<PACKED>(b, list, k);
                             if (in_tube(g, a, d, R)) hit(own, g);
                         }
                     }
@@ -380,9 +387,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
             const u32 k1 = i1 + (u32)(i1 < (u32)t1.y ? t1.x : t1.z);
             const int ow0 = t0.w & 0xff, ow1 = t1.w & 0xff;
             const int4 p0 = sp.i4(0, ow0), q0 = sp.i4(1, ow0), p1 = sp.i4(0, ow1), q1 = sp.i4(1, ow1);
-            const int4 g0 = ((t0.w >> 8) ? b.gcy : b.gc)[k0];
+            const int4 g0 = grain_at<PACKED>(b, t0.w >> 8, k0);
             int4 g1 = make_int4(0, 0, 0, 0);
-            if (v1) g1 = ((t1.w >> 8) ? b.gcy : b.gc)[k1];
+            if (v1) g1 = grain_at<PACKED>(b, t1.w >> 8, k1);
             const long long R0 = (long long)(((unsigned long long)(unsigned)q0.w << 32) | (unsigned)q0.z);
             const long long R1 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned)q1.z);
             if (in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
@@ -398,7 +405,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                 const u32 k = i + (u32)(i < (u32)t.y ? t.x : t.z);
                 const int ow = t.w & 0xff;
                 const int4 e0 = sp.i4(0, ow), e1 = sp.i4(1, ow);
-                const int4 g = ((t.w >> 8) ? b.gcy : b.gc)[k];
+                const int4 g = grain_at<PACKED>(b, t.w >> 8, k);
                 const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
                 if (in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R)) hit(ow, g);
             }
@@ -442,8 +449,8 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         }
         scount[wib][lane] = 0;
         __syncwarp();
-        warp_items(b, sp[wib], tbl[wib], n_items, tests,
-                   [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
+        warp_items<true>(b, sp[wib], tbl[wib], n_items, tests,
+                         [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
@@ -531,7 +538,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
         }
         __syncwarp();
         u32 tests = 0;
-        warp_items(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
+        warp_items<false>(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
             members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
         });
         __syncwarp();

@@ -58,6 +58,7 @@ __global__ void k_cell_order(Batch b, const u32 *sorted_vals) {
         const u32 p = sorted_vals[q];
         int4 g = b.gr[p];
         b.gc[q] = make_int4(g.x, g.y, g.z, (int)p);
+        b.gp[q] = pack_xyz(g.x, g.y, g.z);
     }
 }
 
@@ -83,6 +84,7 @@ __global__ void k_cell_order_y(Batch b, const u32 *sorted_vals) {
         const u32 p = sorted_vals[q];
         const int4 g = b.gr[p];
         b.gcy[q] = make_int4(g.x, g.y, g.z, (int)p);
+        b.gpy[q] = pack_xyz(g.x, g.y, g.z);
     }
 }
 

@@ -264,6 +264,8 @@ et_status BatchRT::reserve() {
             gr = c.take<int4>(n);
             gc = c.take<int4>(n);
             gcy = c.take<int4>(n);
+            gp = c.take<u64>(n);
+            gpy = c.take<u64>(n);
             seed_off = c.take<u64>(n + 1);
             best[0] = c.take<u64>(n);
             best[1] = c.take<u64>(n);
@@ -470,11 +472,13 @@ Batch BatchRT::dev_batch() const {
     b.ncelly = (int)ncelly;
     b.dual = dual ? 1 : 0;
     b.gcy = gcy;
+    b.gpy = gpy;
     b.cell_start_y = cell_start_y;
     b.vshift = cbits[0] + cbits[1] + cbits[2];
     b.xyz_in = xyz_in;
     b.gr = gr;
     b.gc = gc;
+    b.gp = gp;
     b.cell_start = cell_start;
     b.ctl = ctl;
     return b;

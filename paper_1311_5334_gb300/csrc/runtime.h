@@ -74,6 +74,7 @@ struct BatchRT {
     u64 *keys[2] = {nullptr, nullptr};
     u32 *vals[2] = {nullptr, nullptr};
     int4 *gr = nullptr, *gc = nullptr;
+    u64 *gp = nullptr, *gpy = nullptr;
     u64 *seed_off = nullptr;
     u64 *best[2] = {nullptr, nullptr};
     int *owner = nullptr;
