@@ -315,7 +315,9 @@ def run_ours(args):
         plain_views_per_s = e2e_val = None
         h2d = d2h = 0
     else:
-        plain_views_per_s, e2e_val, h2d, d2h = extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws)
+        tuning = (tuple(ref_stats["cell"]), batch.tuning["row_lists"] if tuned else args.rows)
+        plain_views_per_s, e2e_val, h2d, d2h = extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws,
+                                                      tuning)
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
@@ -401,13 +403,15 @@ def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batc
             "p99_ms": float(np.percentile(lat, 99)), "views_per_s": n_views / span, "busy_retries": busy[0]}
 
 
-def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws):
-    """Plain one-view-per-launch form and the end-to-end (host buffers) form."""
+def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
+    """Plain one-view-per-launch form and the end-to-end (host buffers) form,
+    both with the cell tuning of the timed batch."""
     import torch
     from paper_1311_5334_gb300 import et
     n_views = len(views)
     # plain form: one view per launch sequence, same views, device-resident
     plain = et.Batch(ctx, params)
+    plain.set_tuning(tuning[0], row_lists=tuning[1])
     plain_ms = 0.0
     n_plain = min(n_views, int(os.environ.get("ET_PLAIN_VIEWS", "256")))
     for k in range(n_plain):
@@ -430,6 +434,7 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws):
     pinned = torch.from_numpy(xyz_h).pin_memory()
     host_view = pinned.numpy()
     eb = et.Batch(ctx, params)
+    eb.set_tuning(tuning[0], row_lists=tuning[1])
     eb.load(host_view, offs)
     eb.find(use_graph=True)
     tr, mem, voff = eb.fetch()
