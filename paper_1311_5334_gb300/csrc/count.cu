@@ -37,10 +37,21 @@ __device__ __forceinline__ void seed_partners(const Batch &b, long long q, F &&f
     const int cy1 = min(b.nc[1] - 1, (g.y + reach) / b.cs[1]);
     const int cz0 = max(0, g.z - reach) / b.cs[2];
     const int cz1 = min(b.nc[2] - 1, (g.z + reach) / b.cs[2]);
-    for (int cz = cz0; cz <= cz1; ++cz)
+    for (int cz = cz0; cz <= cz1; ++cz) {
+        // distance from g to the row's cells along z and y (0 inside): a row
+        // whose cells are all seed_max or farther holds no partner, and within
+        // a row partners lie at most sqrt(seed_max^2 - 1 - dy^2 - dz^2) ahead in x
+        const long long rz = max(0, max(cz * b.cs[2] - g.z, g.z - (cz * b.cs[2] + b.cs[2] - 1)));
         for (int cy = cy0; cy <= cy1; ++cy) {
+            const long long ry = max(0, max(cy * b.cs[1] - g.y, g.y - (cy * b.cs[1] + b.cs[1] - 1)));
+            const long long left = b.smax2 - 1 - ry * ry - rz * rz;   // largest admissible dx^2
+            if (left < 0) continue;
+            int rx = (int)sqrtf((float)left);   // floor(sqrt(left)), corrected below
+            while ((long long)rx * rx > left) --rx;
+            while ((long long)(rx + 1) * (rx + 1) <= left) ++rx;
+            const int cxr = min(cx1, (g.x + rx) / b.cs[0]);
             const int row = (cz * b.nc[1] + cy) * b.nc[0];
-            const u32 e = cs[row + cx1 + 1];
+            const u32 e = cs[row + cxr + 1];
             for (u32 k = cs[row + cx0]; k < e; ++k) {
                 const int4 h = b.gc[k];
                 if (h.w <= g.w) continue;
@@ -49,6 +60,7 @@ __device__ __forceinline__ void seed_partners(const Batch &b, long long q, F &&f
                 if (d2 >= b.smin2 && d2 < b.smax2) f(g.w, h.w);
             }
         }
+    }
 }
 
 __global__ void __launch_bounds__(CT) k_seed_count(Batch b, Work w) {
