@@ -403,6 +403,19 @@ def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batc
             "p99_ms": float(np.percentile(lat, 99)), "views_per_s": n_views / span, "busy_retries": busy[0]}
 
 
+def pinned_array(n, dtype):
+    """A numpy array of n elements in page-locked host memory (through torch)."""
+    import torch
+    dt = np.dtype(dtype)
+    buf = torch.empty(max(1, n) * dt.itemsize, dtype=torch.uint8).pin_memory()
+    arr = buf.numpy().view(dt)[:n]
+    pinned_array.keep.append(buf)
+    return arr
+
+
+pinned_array.keep = []
+
+
 def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
     """Plain one-view-per-launch form and the end-to-end (host buffers) form,
     both with the cell tuning of the timed batch."""
@@ -438,13 +451,16 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
     eb.load(host_view, offs)
     eb.find(use_graph=True)
     tr, mem, voff = eb.fetch()
+    # page-locked result buffers, reused every step as a serving client would
+    out = (pinned_array(2 * len(tr) + 1024, et.TRACK_DTYPE), pinned_array(2 * len(mem) + 4096, np.int32),
+           pinned_array(n_views + 1, np.int64))
     e2e_steps = max(3, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         eb.load(host_view, offs)
         eb.find(use_graph=True)
-        tr, mem, voff = eb.fetch()
+        tr, mem, voff = eb.fetch(out)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     eb.close()
     h2d = xyz_h.nbytes + offs.nbytes
@@ -635,12 +651,16 @@ def frames_extras(args, ctx, fp, frs, gain, thr, raw_d, V, view_bytes, stream, w
     fr = et.Frames(ctx, fp, gain, thr)
     fr.run(host, n_views=V)
     xyz, pulse, voff = fr.fetch()
+    # page-locked result buffers, reused every step as a serving client would
+    n_cap = 2 * len(xyz) + 1024
+    out = (pinned_array(3 * n_cap, np.int32).reshape(n_cap, 3), pinned_array(n_cap, np.int32),
+           pinned_array(V + 1, np.int64))
     steps = max(3, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         fr.run(host, n_views=V)
-        xyz, pulse, voff = fr.fetch()
+        xyz, pulse, voff = fr.fetch(out)
     e2e_s = (time.perf_counter() - t0) / steps
     d2h = xyz.nbytes + pulse.nbytes + voff.nbytes + 64
 

@@ -271,20 +271,27 @@ class Context:
         return Server(self, params, mem_budget_bytes, max_batch_views)
 
 
-def _fetch(fn, h, with_view_offsets=False, n_views=1):
+def _fetch(fn, h, with_view_offsets=False, n_views=1, out=None):
+    """Tracks and members; `out` = (tracks, members[, view_offsets]) arrays to
+    fill when large enough (reused buffers, e.g. page-locked), else new ones."""
     nt, nm = C.c_int64(), C.c_int64()
     st = fn(h, None, None, 0, C.byref(nt), None, 0, C.byref(nm)) if with_view_offsets else \
         fn(h, None, 0, C.byref(nt), None, 0, C.byref(nm))
     if st not in (OK, CAPACITY):
         _check(st)
-    tracks = np.zeros(nt.value, dtype=TRACK_DTYPE)
-    members = np.zeros(nm.value, dtype=np.int32)
+    ot, om = (out[0], out[1]) if out is not None else (None, None)
+    tracks = ot if ot is not None and ot.dtype == TRACK_DTYPE and ot.shape[0] >= nt.value \
+        else np.zeros(nt.value, dtype=TRACK_DTYPE)
+    members = om if om is not None and om.dtype == np.int32 and om.shape[0] >= nm.value \
+        else np.zeros(nm.value, dtype=np.int32)
     if with_view_offsets:
-        voff = np.zeros(n_views + 1, dtype=np.int64)
+        ov = out[2] if out is not None and len(out) > 2 else None
+        voff = ov if ov is not None and ov.dtype == np.int64 and ov.shape[0] >= n_views + 1 \
+            else np.zeros(n_views + 1, dtype=np.int64)
         _check(fn(h, _ptr(voff), _ptr(tracks), nt.value, C.byref(nt), _ptr(members), nm.value, C.byref(nm)))
-        return tracks, members, voff
+        return tracks[:nt.value], members[:nm.value], voff[:n_views + 1]
     _check(fn(h, _ptr(tracks), nt.value, C.byref(nt), _ptr(members), nm.value, C.byref(nm)))
-    return tracks, members
+    return tracks[:nt.value], members[:nm.value]
 
 
 class Batch:
@@ -338,9 +345,9 @@ class Batch:
     def set_profiling(self, on=True):
         _check(lib().et_batch_set_profiling(self._h, 1 if on else 0))
 
-    def fetch(self):
-        """(tracks, members, view_track_offsets)."""
-        return _fetch(lib().et_batch_fetch, self._h, True, self.n_views)
+    def fetch(self, out=None):
+        """(tracks, members, view_track_offsets); out: optional arrays to reuse."""
+        return _fetch(lib().et_batch_fetch, self._h, True, self.n_views, out)
 
     def stats(self):
         s = Stats()
@@ -392,9 +399,9 @@ class View(Batch):
         else:
             _check(lib().et_track_find(self._h, _stream_ptr(stream)))
 
-    def fetch(self):
-        """(tracks structured array, members int32)."""
-        return _fetch(lib().et_track_fetch, self._h)
+    def fetch(self, out=None):
+        """(tracks structured array, members int32); out: optional arrays to reuse."""
+        return _fetch(lib().et_track_fetch, self._h, out=out)
 
     def seed_counts(self):
         """All seeds (seed_i, seed_j, count) of the last run, unordered."""
@@ -506,18 +513,23 @@ class Frames:
     def sync(self):
         _check(lib().et_frames_sync(self._h))
 
-    def fetch(self):
+    def fetch(self, out=None):
         """(xyz int32 [n][3], pulse int32 [n], view_offsets int64 [V+1]) in raster
-        order of each view's defining voxels."""
+        order of each view's defining voxels; out: optional (xyz, pulse,
+        view_offsets) arrays to fill when large enough."""
         n = C.c_int64()
         st = lib().et_frames_fetch(self._h, None, None, None, 0, C.byref(n))
         if st not in (OK, CAPACITY):
             _check(st)
-        xyz = np.zeros((n.value, 3), dtype=np.int32)
-        pulse = np.zeros(n.value, dtype=np.int32)
-        voff = np.zeros(self.n_views + 1, dtype=np.int64)
+        ox, op, ov = out if out is not None else (None, None, None)
+        xyz = ox if ox is not None and ox.dtype == np.int32 and ox.shape[0] >= n.value and ox.ndim == 2 \
+            else np.zeros((n.value, 3), dtype=np.int32)
+        pulse = op if op is not None and op.dtype == np.int32 and op.shape[0] >= n.value \
+            else np.zeros(n.value, dtype=np.int32)
+        voff = ov if ov is not None and ov.dtype == np.int64 and ov.shape[0] >= self.n_views + 1 \
+            else np.zeros(self.n_views + 1, dtype=np.int64)
         _check(lib().et_frames_fetch(self._h, _ptr(voff), _ptr(xyz), _ptr(pulse), n.value, C.byref(n)))
-        return xyz, pulse, voff
+        return xyz[:n.value], pulse[:n.value], voff[:self.n_views + 1]
 
     def to_batch(self, batch, stream=None):
         _check(lib().et_frames_to_batch(self._h, batch._h, _stream_ptr(stream)))
