@@ -109,10 +109,12 @@ typedef struct {
 /* Optional tuning.  Zero fields mean "choose automatically".  Results never
  * depend on these values, only the speed does. */
 typedef struct {
-    int32_t cell[3];        /* cell-list edge per axis, coordinate units */
+    int32_t cell[3];        /* cell-list edge per axis, coordinate units; 0: automatic
+                               (s0 * (0.22, 1.1, 1.1), s0 the edge of a cube holding 0.35
+                               grains at the batch's mean density) */
     int32_t block_seeds;    /* reserved */
     int32_t row_lists;      /* 1: one cell list, rows along x; 2: also a list with rows
-                               along y, used by lines whose |w_y| > |w_x|; 0: automatic (1) */
+                               along y, used by lines whose |w_y| > |w_x|; 0: automatic (2) */
     int32_t reserved[3];
 } et_tuning;
 

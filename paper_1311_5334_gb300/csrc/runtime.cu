@@ -130,14 +130,17 @@ BatchRT::~BatchRT() {
 void BatchRT::choose_cells() {
     for (int k = 0; k < 3; ++k) cs[k] = tune.cell[k];
     if (cs[0] <= 0 || cs[1] <= 0 || cs[2] <= 0) {
-        // grains per cell ~ 0.35 at the mean density of the batch
+        // s0: the edge of a cube holding 0.35 grains at the mean density of the
+        // batch; cells are short along the x rows and s0 * 1.1 across them, the
+        // region where timed sweeps find the fastest tube walk
         double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
         double nmean = V > 0 ? (double)N / V : 1.0;
         double rho = std::max(nmean, 1.0) / vol;
         double s = std::cbrt(0.35 / rho);
         s = std::min(std::max(s, 64.0), 4096.0);
+        static const double f[3] = {0.22, 1.1, 1.1};
         for (int k = 0; k < 3; ++k)
-            if (tune.cell[k] <= 0) cs[k] = (int)std::lround(s);
+            if (tune.cell[k] <= 0) cs[k] = std::max(16, (int)std::lround(s * f[k]));
     }
     for (int k = 0; k < 3; ++k) {
         cs[k] = std::max(1, std::min(cs[k], p.extent[k]));
@@ -146,7 +149,7 @@ void BatchRT::choose_cells() {
     ncell = (long long)nc[0] * nc[1] * nc[2];
     // the second list swaps the x and y cell edges, so its rows (along y) are
     // as short as the first list's rows (along x)
-    dual = tune.row_lists == 2;
+    dual = tune.row_lists != 1;   // 0 (automatic) uses both lists
     csy[0] = std::max(1, std::min(cs[1], p.extent[0]));
     csy[1] = std::max(1, std::min(cs[0], p.extent[1]));
     csy[2] = cs[2];

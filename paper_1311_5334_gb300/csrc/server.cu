@@ -5,7 +5,10 @@
 // groups the views waiting in the queue into a micro-batch whose estimated
 // device memory fits the budget, runs the batched path on it and keeps the
 // per-view results until the caller polls them.  While one micro-batch runs,
-// new arrivals accumulate, so the batch size adapts to the arrival rate.
+// new arrivals accumulate, so the batch size adapts to the arrival rate.  Two
+// micro-batches alternate: the next is staged and enqueued behind the running
+// one before the running one's results are collected, so the device does not
+// idle while the host gathers views and splits results.
 #include "runtime.h"
 
 #include <chrono>
@@ -61,9 +64,24 @@ struct ServerRT {
     std::unordered_map<uint64_t, Done> polled;
     bool stop = false;
     std::thread worker;
-    BatchRT *batch = nullptr;
     cudaStream_t stream = nullptr;
     size_t max_pending = 1 << 20;
+
+    // Two micro-batches alternate: while one runs on the device, the worker
+    // gathers and enqueues the next (same stream, so the device runs them back
+    // to back) and then collects the first.  Each slot keeps its own host
+    // staging buffers, valid until its results are fetched.
+    struct Slot {
+        BatchRT *batch = nullptr;
+        std::vector<Pending> take;
+        int32_t *xyz = nullptr;   // page-locked staging of the views' grains
+        size_t xyz_cap = 0;       // in int32 elements
+        std::vector<int64_t> off;
+        int64_t t_admit = 0;
+        et_status status = ET_OK;
+        bool busy = false;
+    };
+    Slot slots[2];
 
     ServerRT(Ctx *c, const et_params &pp, uint64_t b, int mv) : ctx(c), p(pp), budget(b), max_views(mv) {}
 
@@ -71,7 +89,7 @@ struct ServerRT {
         cudaSetDevice(ctx->device);
         cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "server stream");
-        batch = new BatchRT(ctx, p);
+        for (auto &sl : slots) sl.batch = new BatchRT(ctx, p);
         worker = std::thread([this] { run(); });
         return ET_OK;
     }
@@ -83,82 +101,122 @@ struct ServerRT {
         }
         cv_work.notify_all();
         if (worker.joinable()) worker.join();
-        delete batch;
+        for (auto &sl : slots) {
+            delete sl.batch;
+            if (sl.xyz) cudaFreeHost(sl.xyz);
+        }
         if (stream) cudaStreamDestroy(stream);
+    }
+
+    // Moves pending views into sl.take within the memory budget; waits for
+    // arrivals only if `wait` (nothing else is in flight).  False: stop.
+    bool gather(Slot &sl, bool wait) {
+        sl.take.clear();
+        std::unique_lock<std::mutex> g(mu);
+        if (wait) cv_work.wait(g, [this] { return stop || !pending.empty(); });
+        if (stop && pending.empty()) return false;
+        uint64_t bytes = 0;
+        while (!pending.empty() && (int)sl.take.size() < max_views) {
+            uint64_t vb = view_bytes(p, pending.front().n);
+            if (!sl.take.empty() && bytes + vb > budget) break;
+            bytes += vb;
+            sl.take.push_back(std::move(pending.front()));
+            pending.pop_front();
+        }
+        return true;
+    }
+
+    void launch(Slot &sl) {
+        sl.t_admit = now_ns();
+        sl.off.assign(1, 0);
+        for (auto &v : sl.take) sl.off.push_back(sl.off.back() + v.n);
+        const size_t need = (size_t)std::max<int64_t>(3 * sl.off.back(), 3);
+        sl.status = ET_OK;
+        if (need > sl.xyz_cap) {   // grows rarely; the slot's previous run is fetched already
+            if (sl.xyz) cudaFreeHost(sl.xyz);
+            sl.xyz = nullptr;
+            sl.xyz_cap = 0;
+            const size_t cap = need + need / 2;
+            if (cudaHostAlloc((void **)&sl.xyz, cap * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                sl.xyz = nullptr;
+                sl.status = fail(ET_ERR_OOM, "page-locked staging of %zu grains", need / 3);
+            } else {
+                sl.xyz_cap = cap;
+            }
+        }
+        if (sl.status == ET_OK) {
+            size_t o = 0;
+            for (auto &v : sl.take) {
+                if (!v.xyz.empty()) memcpy(sl.xyz + o, v.xyz.data(), v.xyz.size() * sizeof(int32_t));
+                o += v.xyz.size();
+            }
+            sl.status = sl.batch->load(sl.xyz, sl.off.data(), (int)sl.take.size(), false, stream);
+        }
+        if (sl.status == ET_OK) sl.status = sl.batch->find(stream, false);
+        sl.busy = true;
+    }
+
+    void complete(Slot &sl, std::vector<int64_t> &vtrk, std::vector<et_track> &trk, std::vector<int32_t> &mem) {
+        et_status s = sl.status;
+        int64_t nt = 0, nm = 0;
+        vtrk.assign(sl.take.size() + 1, 0);
+        if (s == ET_OK) {
+            s = sl.batch->fetch(vtrk.data(), nullptr, 0, &nt, nullptr, 0, &nm);
+            if (s == ET_ERR_CAPACITY || s == ET_OK) {
+                trk.resize((size_t)std::max<int64_t>(nt, 1));
+                mem.resize((size_t)std::max<int64_t>(nm, 1));
+                s = sl.batch->fetch(vtrk.data(), trk.data(), nt, &nt, mem.data(), nm, &nm);
+            }
+        }
+        const int64_t t_done = now_ns();
+        std::vector<Done> out(sl.take.size());
+        for (size_t v = 0; v < sl.take.size(); ++v) {
+            Done &d = out[v];
+            memset(&d.r, 0, sizeof d.r);
+            d.r.tag = sl.take[v].tag;
+            d.r.status = s;
+            d.r.n_grains = sl.take[v].n;
+            d.r.t_submit_ns = sl.take[v].t_submit;
+            d.r.t_admit_ns = sl.t_admit;
+            d.r.t_done_ns = t_done;
+            if (s == ET_OK) {
+                const int64_t t0 = vtrk[v], t1 = vtrk[v + 1];
+                d.tracks.assign(trk.begin() + t0, trk.begin() + t1);
+                int64_t m0 = t1 > t0 ? trk[t0].member_offset : 0;
+                int64_t m1 = t1 > t0 ? trk[t1 - 1].member_offset + trk[t1 - 1].nhits : 0;
+                d.members.assign(mem.begin() + m0, mem.begin() + m1);
+                for (auto &t : d.tracks) {
+                    t.member_offset -= m0;
+                    t.view = 0;
+                }
+                d.r.n_tracks = (int32_t)(t1 - t0);
+                d.r.n_members = m1 - m0;
+            }
+        }
+        {
+            std::lock_guard<std::mutex> g(mu);
+            for (auto &d : out) done.push_back(std::move(d));
+        }
+        cv_done.notify_all();
+        sl.take.clear();
+        sl.busy = false;
     }
 
     void run() {
         cudaSetDevice(ctx->device);
-        std::vector<Pending> take;
-        std::vector<int32_t> xyz;
-        std::vector<int64_t> off;
         std::vector<int64_t> vtrk;
         std::vector<et_track> trk;
         std::vector<int32_t> mem;
+        int cur = 0;
         for (;;) {
-            take.clear();
-            {
-                std::unique_lock<std::mutex> g(mu);
-                cv_work.wait(g, [this] { return stop || !pending.empty(); });
-                if (stop && pending.empty()) return;
-                uint64_t bytes = 0;
-                while (!pending.empty() && (int)take.size() < max_views) {
-                    uint64_t vb = view_bytes(p, pending.front().n);
-                    if (!take.empty() && bytes + vb > budget) break;
-                    bytes += vb;
-                    take.push_back(std::move(pending.front()));
-                    pending.pop_front();
-                }
-            }
-            const int64_t t_admit = now_ns();
-            off.assign(1, 0);
-            xyz.clear();
-            for (auto &v : take) {
-                xyz.insert(xyz.end(), v.xyz.begin(), v.xyz.end());
-                off.push_back(off.back() + v.n);
-            }
-            et_status s = batch->load(xyz.data(), off.data(), (int)take.size(), false, stream);
-            if (s == ET_OK) s = batch->find(stream, false);
-            int64_t nt = 0, nm = 0;
-            vtrk.assign(take.size() + 1, 0);
-            if (s == ET_OK) {
-                s = batch->fetch(vtrk.data(), nullptr, 0, &nt, nullptr, 0, &nm);
-                if (s == ET_ERR_CAPACITY || s == ET_OK) {
-                    trk.resize((size_t)std::max<int64_t>(nt, 1));
-                    mem.resize((size_t)std::max<int64_t>(nm, 1));
-                    s = batch->fetch(vtrk.data(), trk.data(), nt, &nt, mem.data(), nm, &nm);
-                }
-            }
-            const int64_t t_done = now_ns();
-            std::vector<Done> out(take.size());
-            for (size_t v = 0; v < take.size(); ++v) {
-                Done &d = out[v];
-                memset(&d.r, 0, sizeof d.r);
-                d.r.tag = take[v].tag;
-                d.r.status = s;
-                d.r.n_grains = take[v].n;
-                d.r.t_submit_ns = take[v].t_submit;
-                d.r.t_admit_ns = t_admit;
-                d.r.t_done_ns = t_done;
-                if (s == ET_OK) {
-                    const int64_t t0 = vtrk[v], t1 = vtrk[v + 1];
-                    d.tracks.assign(trk.begin() + t0, trk.begin() + t1);
-                    int64_t m0 = t1 > t0 ? trk[t0].member_offset : 0;
-                    int64_t m1 = t1 > t0 ? trk[t1 - 1].member_offset + trk[t1 - 1].nhits : 0;
-                    d.members.assign(mem.begin() + m0, mem.begin() + m1);
-                    for (auto &t : d.tracks) {
-                        t.member_offset -= m0;
-                        t.view = 0;
-                    }
-                    d.r.n_tracks = (int32_t)(t1 - t0);
-                    d.r.n_members = m1 - m0;
-                }
-            }
-            {
-                std::lock_guard<std::mutex> g(mu);
-                for (auto &d : out) done.push_back(std::move(d));
-            }
-            cv_done.notify_all();
+            Slot &sl = slots[cur], &other = slots[cur ^ 1];
+            // wait for arrivals only when nothing is in flight
+            const bool live = gather(sl, !other.busy);
+            if (!sl.take.empty()) launch(sl);
+            if (other.busy) complete(other, vtrk, trk, mem);
+            if (!live && !sl.busy && !other.busy) return;
+            cur ^= 1;
         }
     }
 };
