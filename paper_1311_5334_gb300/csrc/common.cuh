@@ -70,7 +70,8 @@ struct Batch {
     // arrays
     const int *xyz_in;   // N x 3 input, caller order
     int4 *gr;            // canonical order: x, y, z, caller index within the view
-    int4 *gc;            // cell order: x, y, z, canonical (global) index
+    int4 *gc;            // cell order: x, y, z, canonical (global) index; the y-row
+                         // list's order follows at gc + N (gcy)
     u64 *gp;             // cell order: x | y << 21 | z << 42 (the tube counts' 8-byte grain loads)
     u32 *cell_start;     // V * ncell + 1
     // second cell list with rows along y: cell edges (cs[1], cs[0], cs[2]),

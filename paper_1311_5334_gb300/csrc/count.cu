@@ -257,12 +257,13 @@ __device__ __forceinline__ int seed_setup(const Batch &b, int4 ga, int4 gb, int 
 // in this pass (an OR-reduction of one-hot start bits and a popcount) and reads
 // the range from a per-warp table (tbl) indexed by that rank.  So every pass
 // tests 32 grains, however unevenly the rows of the round hold them.
-// Grain k of the x-row (list 0) or y-row (list 1) cell order: 8-byte packed
-// coordinates (PACKED, w = 0) or the 16-byte record with the canonical index.
+// Grain k of the two cell orders back to back (k < N: x-row list, k >= N:
+// y-row list): 8-byte packed coordinates (PACKED, w = 0) or the 16-byte
+// record with the canonical index.
 template <bool PACKED>
-__device__ __forceinline__ int4 grain_at(const Batch &b, int list, u32 k) {
-    if (PACKED) return unpack_xyz((list ? b.gpy : b.gp)[k]);
-    return (list ? b.gcy : b.gc)[k];
+__device__ __forceinline__ int4 grain_at(const Batch &b, u32 k) {
+    if (PACKED) return unpack_xyz(b.gp[k]);
+    return b.gc[k];
 }
 
 template <bool PACKED, class Hit>
@@ -290,7 +291,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
         const int own = before + __popc(smask & lane_le) - 1;
         const int item = ibase + lane;
         u32 b0 = 0, n0 = 0, b1 = 0, n1 = 0;
-        int list = 0;
+        u32 loff = 0;   // N for the y-row list (its cell order follows the x-row one)
         if (item < total) {
             const float4 e2 = sp.f4(2, own), e3 = sp.f4(3, own);
             const int co = __float_as_int(e2.z) + (item - __float_as_int(e2.w));
@@ -300,7 +301,8 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                 const float4 e4 = sp.f4(4, own), e5 = sp.f4(5, own), e6 = sp.f4(6, own);
                 const int4 e7 = sp.i4(7, own);
                 const int flags = __float_as_int(e5.w);
-                list = flags & 1;
+                const int list = flags & 1;
+                loff = list ? (u32)b.N : 0u;
                 const bool ineg = (flags & 2) != 0, rneg = (flags & 4) != 0;
                 // inner cells reached over [ta, tb]
                 const float il = fmaf(ineg ? tb : ta, e5.z, e5.x), ih = fmaf(ineg ? ta : tb, e5.z, e5.y);
@@ -358,7 +360,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                             (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
                         tests += end - beg;
                         for (u32 k = beg; k < end; ++k) {
-                            const int4 g = grain_at<PACKED>(b, list, k);
+                            const int4 g = grain_at<PACKED>(b, loff + k);
                             if (in_tube(g, a, d, R)) hit(own, g);
                         }
                     }
@@ -377,9 +379,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
         const u32 rtotal = __shfl_sync(0xffffffffu, rin, 31);
         const u32 rex = rin - n;
         const unsigned nonempty = __ballot_sync(0xffffffffu, n > 0);
-        if (n > 0)
+        if (n > 0)   // offsets into the two lists back to back
             tbl[__popc(nonempty & lane_lt)] =
-                make_int4((int)(b0 - rex), (int)(rex + n0), (int)(b1 - rex - n0), own | (list << 8));
+                make_int4((int)(b0 + loff - rex), (int)(rex + n0), (int)(b1 + loff - rex - n0), own);
         __syncwarp();
         // two passes per iteration, so that their table, geometry and grain
         // loads overlap; a last part of at most 32 grains takes one pass
@@ -397,11 +399,11 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
             const int4 t1 = tbl[v1 ? bef1 + __popc(sm1 & lane_le) - 1 : 0];
             const u32 k0 = i0 + (u32)(i0 < (u32)t0.y ? t0.x : t0.z);
             const u32 k1 = i1 + (u32)(i1 < (u32)t1.y ? t1.x : t1.z);
-            const int ow0 = t0.w & 0xff, ow1 = t1.w & 0xff;
+            const int ow0 = t0.w, ow1 = t1.w;
             const int4 p0 = sp.i4(0, ow0), q0 = sp.i4(1, ow0), p1 = sp.i4(0, ow1), q1 = sp.i4(1, ow1);
-            const int4 g0 = grain_at<PACKED>(b, t0.w >> 8, k0);
+            const int4 g0 = grain_at<PACKED>(b, k0);
             int4 g1 = make_int4(0, 0, 0, 0);
-            if (v1) g1 = grain_at<PACKED>(b, t1.w >> 8, k1);
+            if (v1) g1 = grain_at<PACKED>(b, k1);
             const long long R0 = (long long)(((unsigned long long)(unsigned)q0.w << 32) | (unsigned)q0.z);
             const long long R1 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned)q1.z);
             if (in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
@@ -415,9 +417,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
             if (i < rtotal) {
                 const int4 t = tbl[bef + __popc(sm & lane_le) - 1];
                 const u32 k = i + (u32)(i < (u32)t.y ? t.x : t.z);
-                const int ow = t.w & 0xff;
+                const int ow = t.w;
                 const int4 e0 = sp.i4(0, ow), e1 = sp.i4(1, ow);
-                const int4 g = grain_at<PACKED>(b, t.w >> 8, k);
+                const int4 g = grain_at<PACKED>(b, k);
                 const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
                 if (in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R)) hit(ow, g);
             }

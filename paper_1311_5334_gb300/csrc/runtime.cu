@@ -265,10 +265,12 @@ et_status BatchRT::reserve() {
             vals[0] = c.take<u32>(n);
             vals[1] = c.take<u32>(n);
             gr = c.take<int4>(n);
-            gc = c.take<int4>(n);
-            gcy = c.take<int4>(n);
-            gp = c.take<u64>(n);
-            gpy = c.take<u64>(n);
+            // the two cell orders back to back (the y-row list at offset n), so a
+            // walk addresses either through one array
+            gc = c.take<int4>(2 * n);
+            gcy = gc ? gc + n : nullptr;
+            gp = c.take<u64>(2 * n);
+            gpy = gp ? gp + n : nullptr;
             seed_off = c.take<u64>(n + 1);
             best[0] = c.take<u64>(n);
             best[1] = c.take<u64>(n);
