@@ -111,7 +111,7 @@ __device__ __forceinline__ u64 ticket_size(u64 n) {
 }
 
 // Cover geometry of one line, resolved once per line into eight 16-byte
-// vectors (loaded with eight vector loads per work item).  Slab t-intervals
+// vectors (an item loads the six it needs, a grain test the first two).  Slab t-intervals
 // are kept as (lower end at cell 0, step per cell, width) with the direction's
 // sign already folded in, so the walk needs no min/max to order their ends.
 struct __align__(16) SeedSm {
