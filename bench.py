@@ -42,9 +42,9 @@ METRIC = "views/s"
 # 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
 OPS_PER_TEST = 14
 # DRAM bytes the tube-count kernel moves per seed (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture on the dense view: 21.96 MB for
+# dram__bytes_write.sum of one ncu capture on the dense view: 21.73 MB for
 # 2,571,392 seeds); a launch's traffic is scaled by its seed count.
-TUBE_DRAM_BYTES_PER_SEED = (21.964032e6 + 256) / 2571392
+TUBE_DRAM_BYTES_PER_SEED = 21.731584e6 / 2571392
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
