@@ -105,6 +105,7 @@ struct Work {
     u64 *best[2];        // per grain
     int *owner;          // per grain: accepting candidate or -1
     int *clist[2];       // undecided candidates carried to the next round (cand_cap each)
+    const u32 *corder;   // candidates in key order (the association's windows)
     // diagnostic per-seed record (optional)
     int *rec_lo, *rec_hi, *rec_cnt;
     u64 rec_cap;
@@ -180,6 +181,7 @@ void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t s
 void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st);
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st);
 void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st);
+const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st);
 
 // merge.cu
 int merge_grid_blocks(int device);

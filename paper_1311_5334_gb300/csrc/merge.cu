@@ -21,6 +21,13 @@
 // resets the slots it holds; one still undecided resets last round's slots of
 // all its grains at the start of the next round.
 //
+// A candidate is only ever blocked by candidates of smaller key, so the
+// rounds run over windows of the key-sorted candidate list, one window after
+// the other: a window's candidates are decided with every earlier window
+// already final and no later one taking part.  The result is the same; a
+// candidate joins only the rounds of its own window instead of every round
+// until its decision.
+//
 // Rounds are separated by a grid barrier in one cooperative launch; every
 // wait is bounded and a timeout sets ERRB_TIMEOUT instead of hanging.
 #include "common.cuh"
@@ -82,25 +89,30 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const u32 H = (u32)b.H;
     __shared__ int keep[MT / 32][32];   // per warp: undecided candidates waiting to be appended
-    for (u32 round = 0;; ++round) {
+    const u64 win = max((u64)1 << 20, (nc + 31) / 32);   // candidates per window
+    u32 round = 0;   // counts all rounds: it selects the ping-pong buffers
+    for (u64 w0 = 0; w0 < nc; w0 += win) {
+    const u64 w1 = min(nc, w0 + win);
+    for (u32 wr = 0;; ++wr, ++round) {
         u64 *B = w.best[round & 1];
         u64 *Bp = w.best[(round + 1) & 1];
-        // candidates of this round: all of them first, then the carried list
-        const int *list = round == 0 ? nullptr : w.clist[round & 1];
-        const long long nl = round == 0 ? (long long)nc : (long long)__ldcg(&ctl->ncl[round & 1]);
+        // candidates of this round: the window first, then the carried list
+        const bool first = wr == 0;
+        const int *list = first ? nullptr : w.clist[round & 1];
+        const long long nl = first ? (long long)(w1 - w0) : (long long)__ldcg(&ctl->ncl[round & 1]);
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->ncl[(round + 1) & 1] = 0;
         // ---- phase 1: reject hopeless candidates, post keys on unused grains
         u32 my_active = 0;
         for (long long i = gwarp; i < nl; i += nwarps) {
             // lists and states are rewritten by other SMs between rounds: read through L2
-            const long long c = list ? __ldcg(&list[i]) : i;
+            const long long c = list ? __ldcg(&list[i]) : (long long)w.corder[w0 + i];
             if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             if (m1 - m0 <= 32) {   // one chunk: member and its state stay in registers
                 const u64 m = m0 + lane;
                 const bool in = m < m1;
                 const int g = in ? w.members[m] : 0;
-                if (in && round > 0) Bp[g] = ~0ull;
+                if (in && !first) Bp[g] = ~0ull;
                 const bool fr = in && __ldcg(&w.owner[g]) < 0;
                 const u32 nfree = __popc(__ballot_sync(0xffffffffu, fr));
                 if (nfree < H) {
@@ -116,7 +128,7 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
                 const u64 m = base + lane;
                 const bool in = m < m1;
                 const int g = in ? w.members[m] : 0;
-                if (in && round > 0) Bp[g] = ~0ull;   // entries this candidate posted last round
+                if (in && !first) Bp[g] = ~0ull;   // entries this candidate posted last round
                 const bool fr = in && __ldcg(&w.owner[g]) < 0;
                 nfree += __popc(__ballot_sync(0xffffffffu, fr));
             }
@@ -138,17 +150,19 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
         if (!grid_barrier(ctl, gridDim.x)) return;
         const u32 active = ld_cg_u32(&ctl->active[round & 1]);
         if (blockIdx.x == 0 && threadIdx.x == 0 && round < 64) ctl->round_active[round] = active;
-        if (active == 0) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
-            return;
-        }
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->active[(round + 1) & 1] = 0;
+        if (active == 0) {   // the window is decided (uniform: every block read the same count)
+            ++round;
+            // the next window's first round counts into the counter just reset
+            if (!grid_barrier(ctl, gridDim.x)) return;
+            break;
+        }
         // ---- phase 2: accept ready candidates, carry the others to the next round
         int *next = w.clist[(round + 1) & 1];
         u64 *next_n = &ctl->ncl[(round + 1) & 1];
         int nkeep = 0;   // warp-uniform
         for (long long i = gwarp; i < nl; i += nwarps) {
-            const long long c = list ? __ldcg(&list[i]) : i;
+            const long long c = list ? __ldcg(&list[i]) : (long long)w.corder[w0 + i];
             if (__ldcg(&w.c_state[c]) != CS_UNDECIDED) continue;
             const u64 m0 = w.c_moff[c], m1 = w.c_moff[c + 1];
             const u64 key = w.c_key[c];
@@ -239,6 +253,19 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             __syncwarp();
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
+    }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
+}
+
+// Candidate keys and indices, sorted by key (the association's windows).
+__global__ void k_cand_sort_in(Batch b, Work w, u64 *k, u32 *v) {
+    if (input_failed(b.ctl)) return;
+    const u64 nc = min(b.ctl->n_cand, w.cand_cap);
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
+        k[c] = w.c_key[c];
+        v[c] = (u32)c;
     }
 }
 
@@ -526,6 +553,13 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
     Work ww = w;
     void *args[] = {&bb, &ww};
     return cudaLaunchCooperativeKernel((const void *)k_merge, dim3(grid), dim3(MT), args, 0, st);
+}
+
+const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st) {
+    k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
+    const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
+                                         &b.ctl->n_cand, 63, temp, st);
+    return o.sort_v[cur];
 }
 
 void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st) {

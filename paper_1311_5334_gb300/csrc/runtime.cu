@@ -580,7 +580,9 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         if (p.flags & ET_FLAG_SINGLE_PASS) {
             launch_single_pass(b, w, st);
         } else {
-            cudaError_t e = launch_merge_coop(b, w, ctx->merge_grid, st);
+            Work wm = w;
+            wm.corder = launch_cand_order(b, w, o, temp, st);
+            cudaError_t e = launch_merge_coop(b, wm, ctx->merge_grid, st);
             if (e != cudaSuccess) return cuda_fail(e, "merge launch");
         }
         mark(5, st);
