@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const u32 H = (u32)b.H;
     __shared__ int keep[MT / 32][32];   // per warp: undecided candidates waiting to be appended
-    const u64 win = max((u64)1 << 20, (nc + 31) / 32);   // candidates per window
+    const u64 win = max((u64)1 << 18, (nc + 128 - 1) / 128);   // candidates per window
     u32 round = 0;   // counts all rounds: it selects the ping-pong buffers
     for (u64 w0 = 0; w0 < nc; w0 += win) {
     const u64 w1 = min(nc, w0 + win);
