@@ -115,7 +115,10 @@ typedef struct {
     int32_t block_seeds;    /* reserved */
     int32_t row_lists;      /* 1: one cell list, rows along x; 2: also a list with rows
                                along y, used by lines whose |w_y| > |w_x|; 0: automatic (2) */
-    int32_t reserved[3];
+    int32_t assoc_window;   /* candidates per window of the exclusive association (the
+                               rounds run window by window in candidate order); 0: automatic
+                               (at least 2^18, at most 128 windows) */
+    int32_t reserved[2];
 } et_tuning;
 
 /* One reconstructed track.  seed_i / seed_j are indices into the caller's grain

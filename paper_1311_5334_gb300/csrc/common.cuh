@@ -106,6 +106,7 @@ struct Work {
     int *owner;          // per grain: accepting candidate or -1
     int *clist[2];       // undecided candidates carried to the next round (cand_cap each)
     const u32 *corder;   // candidates in key order (the association's windows)
+    u64 window;          // candidates per window (0: automatic)
     // diagnostic per-seed record (optional)
     int *rec_lo, *rec_hi, *rec_cnt;
     u64 rec_cap;

@@ -89,7 +89,8 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const u32 H = (u32)b.H;
     __shared__ int keep[MT / 32][32];   // per warp: undecided candidates waiting to be appended
-    const u64 win = max((u64)1 << 18, (nc + 128 - 1) / 128);   // candidates per window
+    // candidates per window: at least 2^18, at most 128 windows, unless set
+    const u64 win = w.window ? w.window : max((u64)1 << 18, (nc + 128 - 1) / 128);
     u32 round = 0;   // counts all rounds: it selects the ping-pong buffers
     for (u64 w0 = 0; w0 < nc; w0 += win) {
     const u64 w1 = min(nc, w0 + win);

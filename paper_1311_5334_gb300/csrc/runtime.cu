@@ -582,6 +582,7 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         } else {
             Work wm = w;
             wm.corder = launch_cand_order(b, w, o, temp, st);
+            wm.window = tune.assoc_window > 0 ? (u64)tune.assoc_window : 0;
             cudaError_t e = launch_merge_coop(b, wm, ctx->merge_grid, st);
             if (e != cudaSuccess) return cuda_fail(e, "merge launch");
         }
@@ -912,6 +913,7 @@ et_status et_batch_set_tuning(et_batch *b, const et_tuning *t) {
     if (!b || !t) return fail(ET_ERR_INVALID_ARG, "batch/tuning is NULL");
     for (int k = 0; k < 3; ++k)
         if (t->cell[k] < 0) return fail(ET_ERR_INVALID_ARG, "cell[%d] < 0", k);
+    if (t->assoc_window < 0) return fail(ET_ERR_INVALID_ARG, "assoc_window < 0");
     b->tune = *t;
     b->loaded = false;   // the cell grid changes: reload required
     return ET_OK;

@@ -50,7 +50,7 @@ class Params(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("cell", C.c_int32 * 3), ("block_seeds", C.c_int32), ("row_lists", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("assoc_window", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Stats(C.Structure):
@@ -306,11 +306,12 @@ class Batch:
         self._keep = None
         self.n_views = 0
 
-    def set_tuning(self, cell=(0, 0, 0), row_lists=0):
+    def set_tuning(self, cell=(0, 0, 0), row_lists=0, assoc_window=0):
         t = Tuning()
         for k in range(3):
             t.cell[k] = int(cell[k])
         t.row_lists = int(row_lists)
+        t.assoc_window = int(assoc_window)
         _check(lib().et_batch_set_tuning(self._h, C.byref(t)))
 
     def load(self, xyz, offsets, stream=None):

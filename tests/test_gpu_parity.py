@@ -207,6 +207,25 @@ def test_batched_matches_oracle_per_view(et, ctx, oracle_mod):
         b.close()
 
 
+@pytest.mark.parametrize("window", [1, 7, 64, 1000])
+def test_association_windows(et, ctx, oracle_mod, window):
+    # the association runs window by window over the key-sorted candidates;
+    # tiny windows (many window boundaries) give the same tracks
+    for v in (synth.pr1(), synth.dense()):
+        p = synth.params(v.extent)
+        want = oracle_run(oracle_mod, v.xyz, p)
+        view = et.View.create(ctx, v.xyz, p)
+        try:
+            view.set_tuning((0, 0, 0), row_lists=0, assoc_window=window)
+            view.load_host(v.xyz)
+            view.find(use_graph=True)
+            tracks, members = view.fetch()
+            assert view.stats()["merge_rounds"] >= min(want.n_cand, 1000) // window
+        finally:
+            view.close()
+        assert_same(et, tracks, members, want)
+
+
 def test_graph_replay_follows_tuning_changes(et, ctx, oracle_mod):
     # a captured launch sequence must not outlive the cell grid it was captured for
     views = [v for v in synth.batched(n_views=12, seed=3) if v.n < 20000][:6]
