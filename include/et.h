@@ -214,9 +214,9 @@ et_status et_track_fetch(et_view *view, et_track *tracks, int64_t cap, int64_t *
 
 /* Per-seed tube counts of the last run: seeds (seed_i, seed_j, count) for every
  * seed hypothesis, in no particular order (parity checks and diagnostics).
- * Requires ET_FLAG... nothing: the view re-runs the count stage with a record
- * buffer.  Returns ET_ERR_CAPACITY with *n_seeds = required size if cap is
- * too small. */
+ * The view runs the path once more with a per-seed record buffer (no flag or
+ * earlier setup needed).  Returns ET_ERR_CAPACITY with *n_seeds = required
+ * size if cap is too small. */
 et_status et_view_seed_counts(et_view *view, int32_t *seed_i, int32_t *seed_j, int32_t *count,
                               int64_t cap, int64_t *n_seeds);
 
