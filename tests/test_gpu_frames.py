@@ -136,6 +136,17 @@ def test_empty_and_saturated(et, ctx, oracle_mod):
     assert st["n_candidates"] == D * H * W
 
 
+@pytest.mark.parametrize("shape", [(3, 64, 4096), (2, 4096, 300), (1024, 16, 32)])
+def test_geometry_limits(et, ctx, oracle_mod, shape):
+    # widest frames (16 tiles across), tallest (256 tiles down), deepest stack
+    # (1024 frames through the stage ring)
+    D, H, W = shape
+    views = [synth.random_blobs(shape, n=max(8, D * H * W // 2000), seed=71, row_pitch=(W + 15) // 16 * 16)]
+    out, st = run_gpu(et, ctx, views)
+    check(oracle_mod, views, out)
+    assert st["n_voxels"] == D * H * W
+
+
 def test_output_overflow_grows(et, ctx, oracle_mod):
     # isolated maxima every second voxel along each axis: far more grains than
     # the first buffer guess (max(65536, voxels / 2000)) -- the run is repeated

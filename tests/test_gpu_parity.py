@@ -296,6 +296,28 @@ def test_clustered_view_forces_buffer_growth(et, ctx, oracle_mod):
     assert_same(et, tracks, members, want)
 
 
+def test_coordinates_at_the_limit(et, ctx, oracle_mod):
+    # extent 2^21 on every axis: coordinates use all 21 bits (packed grains,
+    # canonical keys); seed_max 400 keeps the cross products in int32
+    E = 1 << 21
+    rng = np.random.default_rng(17)
+    fog = rng.integers(E - 6000, E, size=(400, 3))
+    lines = []
+    for d in [(1, 0, 0), (0, 1, 1), (1, 1, 1), (-1, 2, 1)]:
+        for k in range(12):
+            lines.append([E - 1 - 150 * k * abs(c) if c else E - 1 - 3000 for c in d])
+    xyz = np.unique(np.vstack([fog, np.array(lines)]), axis=0).astype(np.int32)
+    p = dict(extent=(E, E, E), seed_min=100, seed_max=400, tube_r=20, min_hits=6)
+    assert xyz.max() == E - 1
+    # the oracle's hash with cells of 2^16 (its default paper cell would need 10^11 cells here)
+    with oracle_mod.Oracle(xyz, p["extent"], p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"],
+                           cell=(1 << 16, 1 << 16, 1 << 16)) as o:
+        want = o.find_tracks()
+    tracks, members, st, _ = run_view(et, ctx, xyz, p)
+    assert len(want) >= 4
+    assert_same(et, tracks, members, want)
+
+
 def test_input_errors(et, ctx):
     with pytest.raises(et.EtError) as e:
         v = et.View.create(ctx, np.array([[1, 2, 3], [1000, 2, 3]]), _p())
