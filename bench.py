@@ -41,10 +41,11 @@ METRIC = "views/s"
 # One tube-membership test: 3 IADD (offset), 6 IMUL/IMAD (int32 cross product),
 # 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
 OPS_PER_TEST = 14
-# DRAM bytes the tube-count kernel moves per seed (dram__bytes_read.sum +
-# dram__bytes_write.sum of one ncu capture on the dense view: 21.73 MB for
-# 2,571,392 seeds); a launch's traffic is scaled by its seed count.
-TUBE_DRAM_BYTES_PER_SEED = 21.731584e6 / 2571392
+# DRAM bytes the tube-count kernel (seed generation and tube counts) moves per
+# seed (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture on the
+# dense view); a launch's traffic is scaled by its seed count.  None: no
+# capture of the current kernel yet.
+TUBE_DRAM_BYTES_PER_SEED = None
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
@@ -338,9 +339,11 @@ def run_ours(args):
             "wall_s": wall,
             "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak,
-                         "traffic": TUBE_DRAM_BYTES_PER_SEED * ref_stats["n_seeds"],
+                         "traffic": (TUBE_DRAM_BYTES_PER_SEED * ref_stats["n_seeds"]
+                                     if TUBE_DRAM_BYTES_PER_SEED else None),
                          "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
-                                  f"{tube_avg_ms:.3f} ms (in-graph CUDA events); peak = "
+                                  f"{tube_avg_ms:.3f} ms (in-graph CUDA events; the kernel also generates "
+                                  f"the seeds); peak = "
                                   f"{info['sm_count']} SMs x 128 lanes x 2070 MHz"},
             "e2e": {"value": e2e_val, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -154,8 +154,9 @@ typedef struct {
     int32_t kernel_launches;/* kernels one run of the path launches (from its captured graph) */
     int32_t profiled;       /* 1 if stage_ms holds timings of the last run */
     /* with profiling on: CUDA-event time of each stage of the last run, ms:
-     * 0 canonical order + cell list, 1 seeds, 2 tube counts, 3 candidate keys
-     * + member lists, 4 merge, 5 output (order, fit, members) */
+     * 0 canonical order + cell list, 1 (empty: the seeds are generated inside
+     * the tube-count kernel), 2 seeds + tube counts, 3 candidate keys + member
+     * lists, 4 merge, 5 output (order, fit, members) */
     float stage_ms[6];
 } et_stats;
 

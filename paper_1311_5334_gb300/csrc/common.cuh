@@ -16,13 +16,12 @@ typedef unsigned int u32;
 enum : u32 {
     ERRB_OUT_OF_RANGE = 1u << 0,
     ERRB_DUPLICATE = 1u << 1,
-    ERRB_OVF_SEEDS = 1u << 2,
     ERRB_OVF_CAND = 1u << 3,
     ERRB_OVF_MEMBERS = 1u << 4,
     ERRB_TIMEOUT = 1u << 5,
     ERRB_OVF_RECORD = 1u << 6,
     ERRB_INPUT_MASK = ERRB_OUT_OF_RANGE | ERRB_DUPLICATE,
-    ERRB_OVF_MASK = ERRB_OVF_SEEDS | ERRB_OVF_CAND | ERRB_OVF_MEMBERS | ERRB_OVF_RECORD,
+    ERRB_OVF_MASK = ERRB_OVF_CAND | ERRB_OVF_MEMBERS | ERRB_OVF_RECORD,
 };
 
 // Candidate states during the merge.
@@ -30,7 +29,7 @@ enum : unsigned char { CS_UNDECIDED = 0, CS_ACCEPTED = 1, CS_REJECTED = 2 };
 
 // Device control block: counters written by the kernels, read back by the host.
 struct Ctl {
-    u64 n_seeds;        // total seeds (scan result)
+    u64 n_seeds;        // seeds generated (inside the tube-count kernel)
     u64 n_tests;        // tube tests performed
     u64 n_hits;         // sum of counts over seeds
     u64 n_cand;         // candidates appended (may exceed capacity -> overflow bit)
@@ -86,11 +85,8 @@ struct Batch {
     Ctl *ctl;
 };
 
-// Seeds and candidates.
+// Candidates (seeds are generated and walked inside the tube-count kernel).
 struct Work {
-    int2 *seeds;         // (lo, hi) canonical global indices
-    u64 seed_cap;
-    u64 *seed_off;       // per grain (cell order) exclusive offsets, N + 1
     // candidates
     int *c_lo, *c_hi;    // canonical global indices
     u32 *c_cnt;          // tube count
@@ -176,8 +172,6 @@ void launch_y_keys(const Batch &b, u64 *keys, u32 *vals, u32 *cell_count, cudaSt
 void launch_cell_order_y(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
 
 // count.cu
-void launch_seed_count(const Batch &b, const Work &w, cudaStream_t st);
-void launch_seed_fill(const Batch &b, const Work &w, cudaStream_t st);
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st);
 void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st);
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st);

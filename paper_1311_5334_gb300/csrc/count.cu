@@ -15,75 +15,30 @@ namespace et {
 
 namespace {
 
-constexpr int CT = 256;
-
 __device__ __forceinline__ u64 warp_sum_u64(u64 v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Visits the partners of the grain at cell-order position q.
-template <class F>
-__device__ __forceinline__ void seed_partners(const Batch &b, long long q, F &&f) {
-    const int4 g = b.gc[q];
-    const int v = view_of(b.goff, b.V, g.w);
-    const u32 *cs = b.cell_start + (size_t)v * b.ncell;
-    const int reach = b.smax - 1;
-    if (reach < 0) return;
-    const int cx0 = g.x / b.cs[0];
-    const int cx1 = min(b.nc[0] - 1, (g.x + reach) / b.cs[0]);
-    const int cy0 = max(0, g.y - reach) / b.cs[1];
-    const int cy1 = min(b.nc[1] - 1, (g.y + reach) / b.cs[1]);
-    const int cz0 = max(0, g.z - reach) / b.cs[2];
-    const int cz1 = min(b.nc[2] - 1, (g.z + reach) / b.cs[2]);
-    for (int cz = cz0; cz <= cz1; ++cz) {
-        // distance from g to the row's cells along z and y (0 inside): a row
-        // whose cells are all seed_max or farther holds no partner, and within
-        // a row partners lie at most sqrt(seed_max^2 - 1 - dy^2 - dz^2) ahead in x
-        const long long rz = max(0, max(cz * b.cs[2] - g.z, g.z - (cz * b.cs[2] + b.cs[2] - 1)));
-        for (int cy = cy0; cy <= cy1; ++cy) {
-            const long long ry = max(0, max(cy * b.cs[1] - g.y, g.y - (cy * b.cs[1] + b.cs[1] - 1)));
-            const long long left = b.smax2 - 1 - ry * ry - rz * rz;   // largest admissible dx^2
-            if (left < 0) continue;
-            int rx = (int)sqrtf((float)left);   // floor(sqrt(left)), corrected below
-            while ((long long)rx * rx > left) --rx;
-            while ((long long)(rx + 1) * (rx + 1) <= left) ++rx;
-            const int cxr = min(cx1, (g.x + rx) / b.cs[0]);
-            const int row = (cz * b.nc[1] + cy) * b.nc[0];
-            const u32 e = cs[row + cxr + 1];
-            for (u32 k = cs[row + cx0]; k < e; ++k) {
-                const int4 h = b.gc[k];
-                if (h.w <= g.w) continue;
-                const long long dx = h.x - g.x, dy = h.y - g.y, dz = h.z - g.z;
-                const long long d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 >= b.smin2 && d2 < b.smax2) f(g.w, h.w);
-            }
-        }
-    }
+// Work tickets of the warp-balanced walks below.
+constexpr int TW = 8;   // warps per block
+constexpr int SEED_CHUNK = 32 * 8;   // largest work ticket of a warp (lines)
+
+// Ticket size: SEED_CHUNK lines, smaller when there are too few lines to give
+// every warp of the grid a few tickets.
+__device__ __forceinline__ u64 ticket_size(u64 n) {
+    const u64 unit = 32;
+    u64 c = (n / ((u64)gridDim.x * TW * 4) + unit - 1) / unit * unit;
+    return c < unit ? unit : (c > (u64)SEED_CHUNK ? (u64)SEED_CHUNK : c);
 }
 
-__global__ void __launch_bounds__(CT) k_seed_count(Batch b, Work w) {
-    if (input_failed(b.ctl)) return;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < b.N; q += stride) {
-        u64 n = 0;
-        seed_partners(b, q, [&](int, int) { ++n; });
-        w.seed_off[q] = n;
-    }
-}
-
-__global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
-    if (input_failed(b.ctl)) return;
-    if (b.ctl->n_seeds > w.seed_cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&b.ctl->error, ERRB_OVF_SEEDS);
-        return;
-    }
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < b.N; q += stride) {
-        u64 o = w.seed_off[q];
-        seed_partners(b, q, [&](int lo, int hi) { w.seeds[o++] = make_int2(lo, hi); });
-    }
+// floor(sqrt(v)) for 0 <= v < 2^62: the float estimate, corrected exactly.
+__device__ __forceinline__ int isqrt_ll(long long v) {
+    int r = (int)sqrtf((float)v);
+    while ((long long)r * r > v) --r;
+    while ((long long)(r + 1) * (r + 1) <= v) ++r;
+    return r;
 }
 
 // Tube walks with warp-level load balancing (tube counts and member lists).
@@ -99,17 +54,6 @@ __global__ void __launch_bounds__(CT) k_seed_fill(Batch b, Work w) {
 // is resolved once into shared memory; per-line results are merged with
 // shared-memory atomics.  The geometry is the conservative cover of
 // tube_cover() (tube.cuh), with the per-slab terms hoisted.
-constexpr int TW = 8;   // warps per block
-constexpr int SEED_CHUNK = 32 * 8;   // largest work ticket of a warp (lines)
-
-// Ticket size: SEED_CHUNK lines, smaller when there are too few lines to give
-// every warp of the grid a few tickets.
-__device__ __forceinline__ u64 ticket_size(u64 n) {
-    const u64 unit = 32;
-    u64 c = (n / ((u64)gridDim.x * TW * 4) + unit - 1) / unit * unit;
-    return c < unit ? unit : (c > (u64)SEED_CHUNK ? (u64)SEED_CHUNK : c);
-}
-
 // Cover geometry of one line, resolved once per line into eight 16-byte
 // vectors (an item loads the six it needs, a grain test the first two).  Slab t-intervals
 // are kept as (lower end at cell 0, step per cell, width) with the direction's
@@ -428,35 +372,185 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
     }
 }
 
+// Seed generation inside the tube-count kernel.
+//
+// Seeds (Section 2) are the pairs of grains of one view with
+// seed_min^2 <= |g_b - g_a|^2 < seed_max^2, each pair once (a of lower
+// canonical rank).  A warp takes SG origins a at a time (consecutive in the
+// x-row cell order, one work ticket).  The cell rows that can hold their
+// partners -- the (y, z) cells within seed_max - 1 of a, each an x run from
+// a's cell to the largest admissible dx -- are dealt to the lanes in rounds
+// of 32, and the grains of a round's rows are tested 32 per pass (owner row
+// found from one-hot start bits, as in the tube walk).  Accepted pairs queue
+// in shared memory; the tube walk takes them 32 at a time.  So seeds are
+// walked in the order origin, row, x, and concurrently running warps work on
+// nearby origins: no seed list is written to memory.
+constexpr int SG = 2;          // origins per work ticket (small: even a one-view batch fills the grid)
+constexpr int SQ = 64;         // seed queue: < 32 waiting + one pass
+
+struct GenSm {
+    int4 og[SG];      // origin: x, y, z, canonical index
+    int4 oc[SG];      // cx0, cx1, cy0, cz0
+    int2 on[SG];      // y cells per z slab, cell-table offset of the view
+    int ofirst[SG];   // first row item of each origin (the group's total if none)
+    int2 tbl[32];     // round's non-empty rows: first position minus pass position, owner origin
+    uint2 rr[32];     // per lane: pass position and length of the lane's row in the round
+    int2 q[SQ];       // seeds waiting for the tube walk (lo, hi)
+};
+
+struct GenState {
+    int gtotal = 0;   // row items of the current origin group
+    int ibase = 0;    // first row item of the current round
+    u32 rtotal = 0;   // grains of the current round
+    u32 pbase = 0;    // next pass position in the round
+    u32 cnt = 0;      // queued seeds
+};
+
+// Takes the next SG origins; false when none is left.
+__device__ __forceinline__ bool gen_group(const Batch &b, GenSm &sm, GenState &gs) {
+    const int lane = threadIdx.x & 31;
+    u64 g0 = 0;
+    if (lane == 0) g0 = atomicAdd(&b.ctl->ticket[0], (u64)SG);
+    g0 = __shfl_sync(0xffffffffu, g0, 0);
+    const u64 N = (u64)b.N;
+    if (g0 >= N) return false;
+    const int reach = b.smax - 1;   // >= 0: seed_max >= 1
+    int nrows = 0;
+    if (lane < SG && g0 + lane < N) {
+        const int4 g = b.gc[g0 + lane];
+        const int v = view_of(b.goff, b.V, g.w);
+        const int cx0 = g.x / b.cs[0];
+        const int cx1 = min(b.nc[0] - 1, (g.x + reach) / b.cs[0]);
+        const int cy0 = max(0, g.y - reach) / b.cs[1];
+        const int cy1 = min(b.nc[1] - 1, (g.y + reach) / b.cs[1]);
+        const int cz0 = max(0, g.z - reach) / b.cs[2];
+        const int cz1 = min(b.nc[2] - 1, (g.z + reach) / b.cs[2]);
+        const int ny = cy1 - cy0 + 1;
+        nrows = ny * (cz1 - cz0 + 1);
+        sm.og[lane] = g;
+        sm.oc[lane] = make_int4(cx0, cx1, cy0, cz0);
+        sm.on[lane] = make_int2(ny, (int)((u32)v * (u32)b.ncell));
+    }
+    int incl = nrows;
+#pragma unroll
+    for (int o = 1; o < SG; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane < SG) sm.ofirst[lane] = incl - nrows;
+    gs.gtotal = __shfl_sync(0xffffffffu, incl, SG - 1);
+    gs.ibase = 0;
+    __syncwarp();
+    return true;
+}
+
+// Resolves the rows of the round at gs.ibase into the pass table.
+__device__ __forceinline__ void gen_round(const Batch &b, GenSm &sm, GenState &gs) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_lt = (1u << lane) - 1u;
+    const int item = gs.ibase + lane;
+    u32 beg = 0, n = 0;
+    int own = 0;
+    if (item < gs.gtotal) {
+        // owner: the last origin whose first item is at or before this one
+        // (an origin without rows has ofirst = gtotal and is never chosen)
+#pragma unroll
+        for (int o = 1; o < SG; ++o) own += sm.ofirst[o] <= item ? 1 : 0;
+        const int4 g = sm.og[own], oc = sm.oc[own];
+        const int2 on = sm.on[own];
+        const int j = item - sm.ofirst[own];
+        const int jz = j / on.x;
+        const int cy = oc.z + (j - jz * on.x), cz = oc.w + jz;
+        const long long rz = max(0, max(cz * b.cs[2] - g.z, g.z - (cz * b.cs[2] + b.cs[2] - 1)));
+        const long long ry = max(0, max(cy * b.cs[1] - g.y, g.y - (cy * b.cs[1] + b.cs[1] - 1)));
+        // the row's nearest point is at least (ry, rz) away in (y, z): it holds
+        // partners only up to dx^2 <= seed_max^2 - 1 - ry^2 - rz^2
+        const long long left = b.smax2 - 1 - ry * ry - rz * rz;
+        if (left >= 0) {
+            const int cxr = min(oc.y, (g.x + isqrt_ll(left)) / b.cs[0]);
+            const u32 *cs = b.cell_start + (u32)on.y + (size_t)(cz * b.nc[1] + cy) * b.nc[0];
+            beg = cs[oc.x];
+            n = cs[cxr + 1] - beg;
+        }
+    }
+    u32 rin = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_up_sync(0xffffffffu, rin, o);
+        if (lane >= o) rin += t;
+    }
+    const u32 rex = rin - n;
+    const unsigned nonempty = __ballot_sync(0xffffffffu, n > 0);
+    if (n > 0) sm.tbl[__popc(nonempty & lane_lt)] = make_int2((int)(beg - rex), own);
+    sm.rr[lane] = make_uint2(rex, n);
+    gs.rtotal = __shfl_sync(0xffffffffu, rin, 31);
+    gs.pbase = 0;
+    __syncwarp();
+}
+
+// One pass of 32 grain tests, appending the accepted pairs to the queue;
+// false when every origin is done.
+__device__ __forceinline__ bool gen_pass(const Batch &b, GenSm &sm, GenState &gs) {
+    while (gs.pbase >= gs.rtotal) {
+        gs.ibase += 32;
+        if (gs.ibase >= gs.gtotal && !gen_group(b, sm, gs)) return false;
+        gen_round(b, sm, gs);
+    }
+    const int lane = threadIdx.x & 31;
+    const unsigned lane_le = 0xffffffffu >> (31 - lane), lane_lt = lane_le >> 1;
+    const uint2 r = sm.rr[lane];
+    const u32 base = gs.pbase;
+    const bool st = r.y > 0 && r.x >= base && r.x < base + 32;
+    const unsigned pm = __reduce_or_sync(0xffffffffu, st ? (1u << (r.x - base)) : 0u);
+    const int bef = __popc(__ballot_sync(0xffffffffu, r.y > 0 && r.x < base));
+    const u32 i = base + lane;
+    bool hit = false;
+    int lo = 0, hi = 0;
+    if (i < gs.rtotal) {
+        const int2 t = sm.tbl[bef + __popc(pm & lane_le) - 1];
+        const int4 h = b.gc[i + (u32)t.x];
+        const int4 g = sm.og[t.y];
+        const long long dx = h.x - g.x, dy = h.y - g.y, dz = h.z - g.z;
+        const long long d2 = dx * dx + dy * dy + dz * dz;
+        hit = h.w > g.w && d2 >= b.smin2 && d2 < b.smax2;
+        lo = g.w;
+        hi = h.w;
+    }
+    const unsigned hm = __ballot_sync(0xffffffffu, hit);
+    if (hit) sm.q[gs.cnt + __popc(hm & lane_lt)] = make_int2(lo, hi);
+    gs.cnt += __popc(hm);
+    gs.pbase = base + 32;
+    __syncwarp();
+    return true;
+}
+
 __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int record) {
     if (input_failed(b.ctl)) return;
-    const u64 ns = b.ctl->n_seeds;
-    if (record && ns > w.rec_cap) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&b.ctl->error, ERRB_OVF_RECORD);
-        return;
-    }
     __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
     __shared__ u32 scount[TW][32];
+    __shared__ GenSm gsm[TW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     u32 tests = 0, hits = 0;   // per thread: far below 2^32 in one launch
-    // warps take contiguous chunks of the seed list (seeds of one view and of
-    // nearby origins) from a ticket counter; no block-wide barrier
-    const u64 tsize = ticket_size(ns);
+    u64 nseeds = 0;            // per warp (lane 0)
+    GenState gs;               // empty: the first pass takes a work ticket
+    bool more = true;
     for (;;) {
-    u64 c0 = 0;
-    if (lane == 0) c0 = atomicAdd(&b.ctl->ticket[0], tsize);
-    c0 = __shfl_sync(0xffffffffu, c0, 0);
-    if (c0 >= ns) break;
-    const u32 len = (u32)min(tsize, ns - c0);
-    for (u32 o = 0; o < len; o += 32) {
-        const bool valid = o + lane < len;
-        const u64 s = c0 + o + lane;
+        while (gs.cnt < 32 && more) more = gen_pass(b, gsm[wib], gs);
+        if (gs.cnt == 0) break;
+        const u32 m = min(gs.cnt, 32u);
+        const bool valid = lane < (int)m;
         int lo = 0, hi = 0, n_items = 0;
         if (valid) {
-            const int2 sd = __ldcs(&w.seeds[s]);   // read once: do not keep in L2
+            const int2 sd = gsm[wib].q[lane];
             lo = sd.x;
             hi = sd.y;
+        }
+        __syncwarp();
+        if (lane + 32 < (int)gs.cnt) gsm[wib].q[lane] = gsm[wib].q[lane + 32];
+        gs.cnt -= m;
+        nseeds += m;
+        if (valid) {
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
             sp[wib].put(lane, q);
@@ -468,20 +562,30 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
-        if (valid && record) {
-            w.rec_lo[s] = b.gr[lo].w;
-            w.rec_hi[s] = b.gr[hi].w;
-            w.rec_cnt[s] = (int)count;
+        if (record) {   // diagnostic per-seed records, appended in blocks of 32
+            u64 r0 = 0;
+            if (lane == 0) r0 = atomicAdd(&b.ctl->n_record, (u64)m);
+            r0 = __shfl_sync(0xffffffffu, r0, 0);
+            if (valid) {
+                const u64 s = r0 + lane;
+                if (s < w.rec_cap) {
+                    w.rec_lo[s] = b.gr[lo].w;
+                    w.rec_hi[s] = b.gr[hi].w;
+                    w.rec_cnt[s] = (int)count;
+                } else {
+                    atomicOr(&b.ctl->error, ERRB_OVF_RECORD);
+                }
+            }
         }
         const bool is_cand = valid && count >= (u32)b.H;
-        const unsigned m = __ballot_sync(0xffffffffu, is_cand);
-        if (m) {
-            const int leader = __ffs(m) - 1;
+        const unsigned cm = __ballot_sync(0xffffffffu, is_cand);
+        if (cm) {
+            const int leader = __ffs(cm) - 1;
             u64 base_idx = 0;
-            if (lane == leader) base_idx = atomicAdd(&b.ctl->n_cand, (u64)__popc(m));
+            if (lane == leader) base_idx = atomicAdd(&b.ctl->n_cand, (u64)__popc(cm));
             base_idx = __shfl_sync(0xffffffffu, base_idx, leader);
             if (is_cand) {
-                const u64 idx = base_idx + __popc(m & ((1u << lane) - 1u));
+                const u64 idx = base_idx + __popc(cm & ((1u << lane) - 1u));
                 if (idx < w.cand_cap) {
                     w.c_lo[idx] = lo;
                     w.c_hi[idx] = hi;
@@ -493,11 +597,11 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         }
         __syncwarp();
     }
-    }
     const u64 wtests = warp_sum_u64(tests), whits = warp_sum_u64(hits);
     if (lane == 0) {
         if (wtests) atomicAdd(&b.ctl->n_tests, wtests);
         if (whits) atomicAdd(&b.ctl->n_hits, whits);
+        if (nseeds) atomicAdd(&b.ctl->n_seeds, nseeds);
     }
 }
 
@@ -572,14 +676,6 @@ unsigned persistent_grid(int blocks_per_sm) {
 }
 
 }  // namespace
-
-void launch_seed_count(const Batch &b, const Work &w, cudaStream_t st) {
-    k_seed_count<<<persistent_grid(8), CT, 0, st>>>(b, w);
-}
-
-void launch_seed_fill(const Batch &b, const Work &w, cudaStream_t st) {
-    k_seed_fill<<<persistent_grid(8), CT, 0, st>>>(b, w);
-}
 
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st) {
     k_tube_count<<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);

@@ -123,7 +123,7 @@ BatchRT::~BatchRT() {
     if (done) cudaEventDestroy(done);
     for (cudaEvent_t &e : ev)
         if (e) cudaEventDestroy(e);
-    for (Group *g : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
+    for (Group *g : {&g_small, &g_grain, &g_cells, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
         g->release(ctx);
 }
 
@@ -236,8 +236,7 @@ void BatchRT::estimate_caps() {
         double n = (double)(goff_h[v + 1] - goff_h[v]);
         s += 0.5 * n * n * frac;
     }
-    u64 seeds = (u64)(1.3 * s) + 4096;
-    want_seeds = std::max(want_seeds, seeds);
+    const u64 seeds = (u64)(1.3 * s) + 4096;   // seeds are not stored: they size the candidates
     want_cand = std::max(want_cand, std::max<u64>(65536, seeds / 16));
     want_members = std::max(want_members, want_cand * 24);
 }
@@ -271,7 +270,6 @@ et_status BatchRT::reserve() {
             gcy = gc ? gc + n : nullptr;
             gp = c.take<u64>(2 * n);
             gpy = gp ? gp + n : nullptr;
-            seed_off = c.take<u64>(n + 1);
             best[0] = c.take<u64>(n);
             best[1] = c.take<u64>(n);
             owner = c.take<int>(n);
@@ -294,12 +292,6 @@ et_status BatchRT::reserve() {
         if (!g_cells.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "cell tables (%zu bytes)", cv.off);
         Carver c2{0, g_cells.base};
         lay(c2);
-    }
-    {
-        size_t need = want_seeds * sizeof(int2);
-        if (!g_seeds.reserve(ctx, align_up(need, 256))) return fail(ET_ERR_OOM, "seeds (%zu bytes)", need);
-        seeds = (int2 *)g_seeds.base;
-        cap_seeds = g_seeds.bytes / sizeof(int2);
     }
     {
         const size_t cc = want_cand;
@@ -374,7 +366,7 @@ et_status BatchRT::reserve() {
 
 unsigned long long BatchRT::layout_generation() const {
     unsigned long long g = 0;
-    for (const Group *x : {&g_small, &g_grain, &g_cells, &g_seeds, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
+    for (const Group *x : {&g_small, &g_grain, &g_cells, &g_cand, &g_members, &g_out, &g_rec, &g_temp})
         g = g * 1315423911ull + x->generation;
     return g;
 }
@@ -397,7 +389,6 @@ unsigned long long BatchRT::graph_signature() const {
     mix((unsigned long long)ncell);
     mix((unsigned long long)ncelly);
     mix(dual ? 1ull : 0ull);
-    mix(cap_seeds);
     mix(cap_cand);
     mix(cap_members);
     mix(cap_rec);
@@ -492,9 +483,6 @@ Batch BatchRT::dev_batch() const {
 Work BatchRT::dev_work() const {
     Work w;
     memset(&w, 0, sizeof w);
-    w.seeds = seeds;
-    w.seed_cap = cap_seeds;
-    w.seed_off = seed_off;
     w.c_lo = c_lo;
     w.c_hi = c_hi;
     w.c_cnt = c_cnt;
@@ -563,10 +551,7 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
             launch_cell_order_y(b, vals[c3], st);
             exclusive_scan_u32(cell_count_y, cell_start_y, (long long)cellsy, temp, st);
         }
-        mark(1, st);
-        launch_seed_count(b, w, st);
-        exclusive_scan_u64(seed_off, seed_off, n, temp, &ctl->n_seeds, st);
-        launch_seed_fill(b, w, st);
+        mark(1, st);   // seeds are generated inside the tube-count kernel: stage 1 stays empty
         mark(2, st);
         launch_tube_count(b, w, record ? 1 : 0, st);
         mark(3, st);
@@ -656,7 +641,6 @@ et_status BatchRT::settle(bool record) {
         if (hctl.error & ERRB_TIMEOUT) return fail(ET_ERR_TIMEOUT, "device-side wait timed out in the merge");
         if (!(hctl.error & ERRB_OVF_MASK)) return ET_OK;
         if (attempt >= 6) return fail(ET_ERR_CAPACITY, "internal buffers kept overflowing");
-        if (hctl.error & ERRB_OVF_SEEDS) want_seeds = std::max<u64>(want_seeds, hctl.n_seeds + 1024);
         if (hctl.error & ERRB_OVF_CAND) {
             want_cand = std::max<u64>(want_cand, hctl.n_cand + 1024);
             want_members = std::max<u64>(want_members, want_cand * 24);

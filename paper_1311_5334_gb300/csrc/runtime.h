@@ -63,11 +63,11 @@ struct BatchRT {
     long long ncelly = 1;
     bool dual = false;
     // requested capacities
-    u64 want_seeds = 0, want_cand = 0, want_members = 0, want_rec = 0;
+    u64 want_cand = 0, want_members = 0, want_rec = 0;
     // granted capacities
-    u64 cap_seeds = 0, cap_cand = 0, cap_members = 0, cap_rec = 0;
+    u64 cap_cand = 0, cap_members = 0, cap_rec = 0;
     // device memory
-    Group g_small, g_grain, g_cells, g_seeds, g_cand, g_members, g_out, g_rec, g_temp;
+    Group g_small, g_grain, g_cells, g_cand, g_members, g_out, g_rec, g_temp;
     Ctl *ctl = nullptr;
     long long *goff = nullptr, *view_trk = nullptr;
     int *xyz_in = nullptr;
@@ -75,14 +75,12 @@ struct BatchRT {
     u32 *vals[2] = {nullptr, nullptr};
     int4 *gr = nullptr, *gc = nullptr;
     u64 *gp = nullptr, *gpy = nullptr;
-    u64 *seed_off = nullptr;
     u64 *best[2] = {nullptr, nullptr};
     int *owner = nullptr;
     int *clist[2] = {nullptr, nullptr};
     u32 *cell_count = nullptr, *cell_start = nullptr;
     u32 *cell_count_y = nullptr, *cell_start_y = nullptr;
     int4 *gcy = nullptr;
-    int2 *seeds = nullptr;
     int *c_lo = nullptr, *c_hi = nullptr;
     u32 *c_cnt = nullptr, *c_nfree = nullptr;
     u64 *c_key = nullptr, *c_moff = nullptr;

@@ -30,13 +30,13 @@ static int64_t now_ns() {
 }
 
 // Device bytes a view of n grains needs inside a batch (same formulas as the
-// batch's own sizing; the seed term dominates).
+// batch's own sizing; seeds are not stored, they size the candidates).
 static uint64_t view_bytes(const et_params &p, int64_t n) {
     const double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
     const double shell = 4.0 / 3.0 * M_PI * (std::pow((double)p.seed_max, 3) - std::pow((double)p.seed_min, 3));
     const double seeds = 1.3 * 0.5 * (double)n * (double)n * std::min(1.0, shell / vol) + 4096;
     const double cand = std::max(65536.0 / 64, seeds / 16);
-    return (uint64_t)(n * 160.0 + seeds * 8.0 + cand * (48.0 + 24 * 4.0) + (1 << 20));
+    return (uint64_t)(n * 160.0 + cand * (48.0 + 24 * 4.0) + (1 << 20));
 }
 
 struct Pending {
