@@ -41,11 +41,14 @@ METRIC = "views/s"
 # One tube-membership test: 3 IADD (offset), 6 IMUL/IMAD (int32 cross product),
 # 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
 OPS_PER_TEST = 14
-# DRAM bytes the tube-count kernel (seed generation and tube counts) moves per
-# seed (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture on the
-# dense view); a launch's traffic is scaled by its seed count.  None: no
-# capture of the current kernel yet.
-TUBE_DRAM_BYTES_PER_SEED = None
+# DRAM bytes one launch of the tube-count kernel (seed generation and tube
+# counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture of that launch (one pass, the first timed step):
+#   batched  706.94 MB + 46.80 MB  (256 views, autotuned cells 74x506x506, both lists)
+# The kernel reads each view's grains and cell tables about once, so the bytes
+# follow the views and the cell shape rather than the seeds; workloads without
+# a capture of their own launch report null.
+TUBE_DRAM_BYTES = {"batched": 706.94e6 + 46.80e6}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
@@ -339,8 +342,7 @@ def run_ours(args):
             "wall_s": wall,
             "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak,
-                         "traffic": (TUBE_DRAM_BYTES_PER_SEED * ref_stats["n_seeds"]
-                                     if TUBE_DRAM_BYTES_PER_SEED else None),
+                         "traffic": TUBE_DRAM_BYTES.get(args.workload),
                          "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
                                   f"{tube_avg_ms:.3f} ms (in-graph CUDA events; the kernel also generates "
                                   f"the seeds); peak = "
@@ -433,7 +435,11 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
     for k in range(n_plain):
         o0, o1 = int(offs[k]), int(offs[k + 1])
         sub = xyz_d[o0:o1]
-        plain.load(sub, [0, o1 - o0], stream=stream)   # warm buffers for this size
+        # warm-up run of this view, settled by fetch: buffers grow to the view's
+        # exact needs, so the timed run cannot overflow and skip work
+        plain.load(sub, [0, o1 - o0], stream=stream)
+        plain.find(stream=stream)
+        plain.fetch()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
