@@ -66,6 +66,7 @@ struct Batch {
     int ncell;           // cells per view
     int cbits[3];        // bit widths of x, y, z in the canonical key
     int vshift;          // bit position of the view index in the canonical key
+    int rbits;           // bit width of a per-view rank or count (largest view's grain count)
     // arrays
     const int *xyz_in;   // N x 3 input, caller order
     int4 *gr;            // canonical order: x, y, z, caller index within the view
@@ -139,6 +140,14 @@ __device__ __forceinline__ int4 unpack_xyz(u64 p) {
     return make_int4((int)(p & 0x1fffffu), (int)((p >> 21) & 0x1fffffu), (int)(p >> 42), 0);
 }
 
+// Sort key of a candidate key (2^21 - 1 - count) << 42 | rank_lo << 21 |
+// rank_hi, in the same order but on 3 * rbits bits: fewer radix passes.
+__device__ __forceinline__ u64 cand_sort_key(const Batch &b, u64 key) {
+    const u64 m21 = (1ull << 21) - 1ull, mr = (1ull << b.rbits) - 1ull;
+    const u64 cnt = m21 - (key >> 42), rlo = (key >> 21) & m21, rhi = key & m21;
+    return ((mr - cnt) << (2 * b.rbits)) | (rlo << b.rbits) | rhi;
+}
+
 __device__ __forceinline__ bool input_failed(const Ctl *ctl) {
     return (*(volatile const u32 *)&ctl->error & (ERRB_INPUT_MASK | ERRB_OVF_MASK | ERRB_TIMEOUT)) != 0;
 }
@@ -165,11 +174,12 @@ int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, co
 
 // grid.cu
 void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st);
-void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u64 *ckeys, u32 *cvals,
-                            u32 *cell_count, cudaStream_t st);
-void launch_cell_order(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
-void launch_y_keys(const Batch &b, u64 *keys, u32 *vals, u32 *cell_count, cudaStream_t st);
-void launch_cell_order_y(const Batch &b, const u32 *sorted_vals, cudaStream_t st);
+void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u32 *cell_of, u32 *cell_count,
+                            cudaStream_t st);
+// cell_start: exclusive scan of the counts; cursor: zeroed per-cell counters
+void launch_cell_scatter(const Batch &b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int ylist,
+                         cudaStream_t st);
+void launch_y_cells(const Batch &b, u32 *cell_of, u32 *cell_count, cudaStream_t st);
 
 // count.cu
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st);

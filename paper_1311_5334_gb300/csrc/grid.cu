@@ -5,7 +5,12 @@
 // candidates, so every result is independent of the caller's grain order and
 // of the cell size.  The cell list bins the grains of each view in a uniform
 // 3D grid (the paper's 3D hash tables, Section 3 footnote), x fastest, so that
-// a run of cells along x is one contiguous range of grains.
+// a run of cells along x is one contiguous range of grains.  The list is a
+// counting sort: per-cell counts, their exclusive scan (cell starts), and a
+// scatter that takes slots with an atomic cursor per cell.  The order of the
+// grains inside one cell is therefore arbitrary; no result depends on it
+// (counts, keys and fits are order-independent, member lists are sorted on
+// output).
 #include "common.cuh"
 
 namespace et {
@@ -30,7 +35,7 @@ __global__ void k_canonical_keys(Batch b, u64 *keys, u32 *vals) {
     }
 }
 
-__global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u64 *ckeys, u32 *cvals,
+__global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u32 *cell_of,
                                   u32 *cell_count) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
@@ -46,24 +51,27 @@ __global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u64
         int cy = min(y / b.cs[1], b.nc[1] - 1);
         int cz = min(z / b.cs[2], b.nc[2] - 1);
         u32 cell = (u32)v * (u32)b.ncell + (u32)(cx + b.nc[0] * (cy + b.nc[1] * cz));
-        ckeys[p] = cell;
-        cvals[p] = (u32)p;
+        cell_of[p] = cell;
         atomicAdd(&cell_count[cell], 1u);
     }
 }
 
-__global__ void k_cell_order(Batch b, const u32 *sorted_vals) {
+// Scatter of the canonical order into a cell list: grain p takes the next
+// slot of its cell (cursor zeroed before the launch).
+__global__ void k_cell_scatter(Batch b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int4 *gc,
+                               u64 *gp) {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < b.N; q += stride) {
-        const u32 p = sorted_vals[q];
-        int4 g = b.gr[p];
-        b.gc[q] = make_int4(g.x, g.y, g.z, (int)p);
-        b.gp[q] = pack_xyz(g.x, g.y, g.z);
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
+        const u32 c = cell_of[p];
+        const u32 q = cell_start[c] + atomicAdd(&cursor[c], 1u);
+        const int4 g = b.gr[p];
+        gc[q] = make_int4(g.x, g.y, g.z, (int)p);
+        gp[q] = pack_xyz(g.x, g.y, g.z);
     }
 }
 
-// Keys of the second cell list (rows along y) for the canonical order.
-__global__ void k_y_keys(Batch b, u64 *keys, u32 *vals, u32 *cell_count) {
+// Cells of the second cell list (rows along y) for the canonical order.
+__global__ void k_y_cells(Batch b, u32 *cell_of, u32 *cell_count) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
         const int v = view_of(b.goff, b.V, p);
@@ -72,19 +80,8 @@ __global__ void k_y_keys(Batch b, u64 *keys, u32 *vals, u32 *cell_count) {
         const int cy = min(g.y / b.csy[1], b.ncy[1] - 1);
         const int cz = min(g.z / b.csy[2], b.ncy[2] - 1);
         const u32 cell = (u32)v * (u32)b.ncelly + (u32)(cy + b.ncy[1] * (cx + b.ncy[0] * cz));
-        keys[p] = cell;
-        vals[p] = (u32)p;
+        cell_of[p] = cell;
         atomicAdd(&cell_count[cell], 1u);
-    }
-}
-
-__global__ void k_cell_order_y(Batch b, const u32 *sorted_vals) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < b.N; q += stride) {
-        const u32 p = sorted_vals[q];
-        const int4 g = b.gr[p];
-        b.gcy[q] = make_int4(g.x, g.y, g.z, (int)p);
-        b.gpy[q] = pack_xyz(g.x, g.y, g.z);
     }
 }
 
@@ -101,21 +98,19 @@ void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st
     k_canonical_keys<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals);
 }
 
-void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u64 *ckeys, u32 *cvals,
-                            u32 *cell_count, cudaStream_t st) {
-    k_canonical_order<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals, ckeys, cvals, cell_count);
+void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u32 *cell_of, u32 *cell_count,
+                            cudaStream_t st) {
+    k_canonical_order<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals, cell_of, cell_count);
 }
 
-void launch_cell_order(const Batch &b, const u32 *sorted_vals, cudaStream_t st) {
-    k_cell_order<<<grid_for(b.N, 256), 256, 0, st>>>(b, sorted_vals);
+void launch_cell_scatter(const Batch &b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int ylist,
+                         cudaStream_t st) {
+    k_cell_scatter<<<grid_for(b.N, 256), 256, 0, st>>>(b, cell_of, cell_start, cursor, ylist ? b.gcy : b.gc,
+                                                       ylist ? b.gpy : b.gp);
 }
 
-void launch_y_keys(const Batch &b, u64 *keys, u32 *vals, u32 *cell_count, cudaStream_t st) {
-    k_y_keys<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals, cell_count);
-}
-
-void launch_cell_order_y(const Batch &b, const u32 *sorted_vals, cudaStream_t st) {
-    k_cell_order_y<<<grid_for(b.N, 256), 256, 0, st>>>(b, sorted_vals);
+void launch_y_cells(const Batch &b, u32 *cell_of, u32 *cell_count, cudaStream_t st) {
+    k_y_cells<<<grid_for(b.N, 256), 256, 0, st>>>(b, cell_of, cell_count);
 }
 
 }  // namespace et

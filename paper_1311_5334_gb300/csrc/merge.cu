@@ -265,7 +265,7 @@ __global__ void k_cand_sort_in(Batch b, Work w, u64 *k, u32 *v) {
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
-        k[c] = w.c_key[c];
+        k[c] = cand_sort_key(b, w.c_key[c]);
         v[c] = (u32)c;
     }
 }
@@ -335,7 +335,7 @@ __global__ void k_collect(Batch b, Work w, Out o) {
         if ((b.flags & ET_FLAG_ANGLE_CUT) && !angle_cut_keeps(b, b.gr[w.c_lo[c]], b.gr[w.c_hi[c]], w.c_nfree[c]))
             continue;
         const u64 i = atomicAdd(&b.ctl->n_acc, 1ull);
-        o.sort_k[0][i] = w.c_key[c];
+        o.sort_k[0][i] = cand_sort_key(b, w.c_key[c]);
         o.sort_v[0][i] = (u32)c;
     }
 }
@@ -440,7 +440,7 @@ __global__ void k_fit(Batch b, Work w, Out o) {
                 s2[0] += dx * dx; s2[1] += dy * dy; s2[2] += dz * dz;
                 s2[3] += dx * dy; s2[4] += dx * dz; s2[5] += dy * dz;
                 const u64 pos = obase + written + __popc(bal & ((1u << lane) - 1u));
-                o.sort_k[0][pos] = ((u64)t << 21) | (u64)p.w;
+                o.sort_k[0][pos] = ((u64)t << b.rbits) | (u64)p.w;
                 o.sort_v[0][pos] = 0u;
             }
             written += __popc(bal);
@@ -518,7 +518,7 @@ __global__ void k_members_out(Batch b, Out o, const u64 *sorted_k) {
     const u64 nm = b.ctl->n_out_members;
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += stride)
-        o.out_members[i] = (int)(sorted_k[i] & ((1ull << 21) - 1ull));
+        o.out_members[i] = (int)(sorted_k[i] & ((1ull << b.rbits) - 1ull));
 }
 
 unsigned sm_count() {
@@ -559,7 +559,7 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
 const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st) {
     k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
     const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
-                                         &b.ctl->n_cand, 63, temp, st);
+                                         &b.ctl->n_cand, 3 * b.rbits, temp, st);
     return o.sort_v[cur];
 }
 
@@ -577,7 +577,8 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     const unsigned g = sm_count() * 4;
     k_collect<<<g, 256, 0, st>>>(b, w, o);
     u64 *na = &b.ctl->n_acc;
-    int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 63, temp, st);
+    int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 3 * b.rbits,
+                                   temp, st);
     if (b.V > 1) {
         k_view_keys<<<g, 256, 0, st>>>(b, w, o.sort_k[cur], o.sort_v[cur]);
         int c2 = radix_sort_pairs_dev(o.sort_k[cur], o.sort_v[cur], o.sort_k[cur ^ 1], o.sort_v[cur ^ 1], acc_cap,
@@ -591,7 +592,7 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_fit<<<g, 256, 0, st>>>(b, w, o);
     const int tbits = bits_for((unsigned long long)(acc_cap > 0 ? acc_cap : 1));
     int cm = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], out_member_cap,
-                                  &b.ctl->n_out_members, 21 + tbits, temp, st);
+                                  &b.ctl->n_out_members, b.rbits + tbits, temp, st);
     k_members_out<<<g, 256, 0, st>>>(b, o, o.sort_k[cm]);
 }
 

@@ -471,6 +471,7 @@ Batch BatchRT::dev_batch() const {
     b.gpy = gpy;
     b.cell_start_y = cell_start_y;
     b.vshift = cbits[0] + cbits[1] + cbits[2];
+    b.rbits = std::max(1, bits_for((unsigned long long)maxN));
     b.xyz_in = xyz_in;
     b.gr = gr;
     b.gc = gc;
@@ -536,20 +537,20 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         launch_canonical_keys(b, keys[0], vals[0], st);
         const int kb = b.vshift + bits_for((unsigned long long)std::max(V - 1, 0));
         int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st);
-        u64 *sk = keys[c1], *ok = keys[c1 ^ 1];
-        u32 *sv = vals[c1], *ov = vals[c1 ^ 1];
-        launch_canonical_order(b, sk, sv, ok, ov, cell_count, st);
-        int c2 = radix_sort_pairs(ok, ov, sk, sv, n, bits_for((unsigned long long)(cells - 1)), temp, st);
-        launch_cell_order(b, c2 ? sv : ov, st);
+        u32 *sv = vals[c1], *cell_of = vals[c1 ^ 1];
+        launch_canonical_order(b, keys[c1], sv, cell_of, cell_count, st);
+        // cell list by counting sort: starts from the counts, then the counts
+        // are zeroed and serve as per-cell cursors of the scatter
         exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st);
+        cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
+        launch_cell_scatter(b, cell_of, cell_start, cell_count, 0, st);
         if (dual) {   // second cell list (rows along y) from the same canonical order
             const size_t cellsy = (size_t)V * (size_t)ncelly;
             cudaMemsetAsync(cell_count_y, 0, sizeof(u32) * cellsy, st);
-            launch_y_keys(b, keys[0], vals[0], cell_count_y, st);
-            int c3 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n,
-                                      bits_for((unsigned long long)(cellsy - 1)), temp, st);
-            launch_cell_order_y(b, vals[c3], st);
+            launch_y_cells(b, cell_of, cell_count_y, st);
             exclusive_scan_u32(cell_count_y, cell_start_y, (long long)cellsy, temp, st);
+            cudaMemsetAsync(cell_count_y, 0, sizeof(u32) * cellsy, st);
+            launch_cell_scatter(b, cell_of, cell_start_y, cell_count_y, 1, st);
         }
         mark(1, st);   // seeds are generated inside the tube-count kernel: stage 1 stays empty
         mark(2, st);
