@@ -307,8 +307,10 @@ def run_ours(args):
     value = whole_job_rate(n_views, ws, ms_per_step)
     seeds_per_s = whole_job_rate(ref_stats["n_seeds"], ws, ms_per_step)
 
-    # roofline of the dominant kernel (tube counts): integer ALU issue
+    # roofline of the dominant kernel (tube counts): integer ALU issue, against
+    # the nominal peak and, beside it, the device's measured integer issue rates
     tube_avg_ms = float(np.mean(tube_ms))
+    int_rates = ctx.int_throughput()
     ops = OPS_PER_TEST * ref_stats["n_tests"]
     achieved = ops / (tube_avg_ms / 1e3) / 1e12
     peak = info["sm_count"] * 128 * 2070e6 / 1e12
@@ -346,7 +348,11 @@ def run_ours(args):
                          "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
                                   f"{tube_avg_ms:.3f} ms (in-graph CUDA events; the kernel also generates "
                                   f"the seeds); peak = "
-                                  f"{info['sm_count']} SMs x 128 lanes x 2070 MHz"},
+                                  f"{info['sm_count']} SMs x 128 lanes x 2070 MHz",
+                         "measured_int_tops": {k: v / 1e12 for k, v in int_rates.items()},
+                         "frac_of_measured_mix": achieved / (int_rates["mix"] / 1e12),
+                         "measured_how": "et_probe_int_throughput: xor+add (alu), a*a+z (mad) and both (mix) "
+                                         "chains, 8 per thread, 2048 threads per SM, CUDA events"},
             "e2e": {"value": e2e_val, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(ref_stats["kernel_launches"]) * args.steps,

@@ -20,7 +20,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libet.so")
 
-SOURCES = ["scan_sort.cu", "grid.cu", "count.cu", "merge.cu", "runtime.cu", "server.cu", "noalloc.cu", "frames.cu"]
+SOURCES = ["scan_sort.cu", "grid.cu", "count.cu", "merge.cu", "runtime.cu", "server.cu", "noalloc.cu", "frames.cu",
+           "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -142,6 +142,7 @@ _SIGS = {
     "et_server_destroy": (C.c_int32, [C.c_void_p]),
     "et_tube_count_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(Params), C.c_void_p, C.c_int64,
                                           C.c_void_p, C.c_void_p]),
+    "et_probe_int_throughput": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double * 3)]),
     "et_frames_create": (C.c_int32, [C.c_void_p, C.POINTER(FrameParams), C.c_void_p, C.c_void_p,
                                      C.POINTER(C.c_void_p)]),
     "et_frames_set_calibration": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -246,6 +247,13 @@ class Context:
         sm, ma, mi = C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().et_ctx_info(self._h, C.byref(sm), C.byref(ma), C.byref(mi)))
         return {"sm_count": sm.value, "cc": (ma.value, mi.value)}
+
+    def int_throughput(self):
+        """Measured 32-bit integer issue rates of the device, ops/s (et_probe.h):
+        {"alu": xor + add, "mad": multiply-add, "mix": both in the tube test's ratio}."""
+        out = (C.c_double * 3)()
+        _check(lib().et_probe_int_throughput(self._h, C.byref(out)))
+        return {"alu": out[0], "mad": out[1], "mix": out[2]}
 
     def close(self):
         if getattr(self, "_h", None):
