@@ -157,9 +157,10 @@ __device__ __forceinline__ bool input_failed(const Ctl *ctl) {
 size_t radix_temp_bytes(long long n);
 // Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key.
 // Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
-// (k0, v0), 1 if in (k1, v1).
+// (k0, v0), 1 if in (k1, v1).  A pass whose tile waits past its limit for a
+// predecessor sets err_bit in *err (the result is then invalid).
 int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp,
-                     cudaStream_t st);
+                     cudaStream_t st, u32 *err, u32 err_bit);
 size_t scan_temp_bytes(long long n);
 // Exclusive prefix sum of n values; writes n + 1 outputs (the last = total).
 // If total_out != nullptr the total is also stored there.  In place allowed.
@@ -170,7 +171,9 @@ void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaSt
 void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
                             u64 *total_out, cudaStream_t st);
 int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,
-                         void *temp, cudaStream_t st);
+                         void *temp, cudaStream_t st, u32 *err, u32 err_bit);
+// Kernel launches of one radix sort on bits bits (histogram, bases, passes).
+inline int radix_sort_launches(int bits) { return bits > 0 ? 2 + (bits + 7) / 8 : 0; }
 
 // grid.cu
 void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st);

@@ -548,10 +548,9 @@ struct FramesRT {
         cudaEventRecord(ev[2], st);
         const int bits = bits_for((u64)V * p.depth * p.height * p.width - 1);
         sorted = radix_sort_pairs_dev(keys[0], vals[0], keys[1], vals[1], (long long)cap, &ctl->n_grains, bits,
-                                      temp, st);
-        // recognition, per 8-bit sort pass a histogram, a 3-kernel scan and a
-        // scatter, the gather and the 3-kernel scan of the view counts
-        launches = 1 + 5 * ((bits + 7) / 8) + 1 + 3;
+                                      temp, st, &ctl->error, FRB_TIMEOUT);
+        // recognition, the sort, the gather and the 3-kernel scan of the view counts
+        launches = 1 + radix_sort_launches(bits) + 1 + 3;
         k_fr_gather<<<152 * 4, 256, 0, st>>>(ctl, cap, vals[sorted], rec, xyz, pulse);
         exclusive_scan_u32(view_count, view_off, (long long)V, temp, st);   // view_off[V] = total
         cudaError_t e = cudaGetLastError();

@@ -559,7 +559,7 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
 const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st) {
     k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
     const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
-                                         &b.ctl->n_cand, 3 * b.rbits, temp, st);
+                                         &b.ctl->n_cand, 3 * b.rbits, temp, st, &b.ctl->error, ERRB_TIMEOUT);
     return o.sort_v[cur];
 }
 
@@ -578,11 +578,11 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_collect<<<g, 256, 0, st>>>(b, w, o);
     u64 *na = &b.ctl->n_acc;
     int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 3 * b.rbits,
-                                   temp, st);
+                                   temp, st, &b.ctl->error, ERRB_TIMEOUT);
     if (b.V > 1) {
         k_view_keys<<<g, 256, 0, st>>>(b, w, o.sort_k[cur], o.sort_v[cur]);
         int c2 = radix_sort_pairs_dev(o.sort_k[cur], o.sort_v[cur], o.sort_k[cur ^ 1], o.sort_v[cur ^ 1], acc_cap,
-                                      na, bits_for((unsigned long long)(b.V - 1)), temp, st);
+                                      na, bits_for((unsigned long long)(b.V - 1)), temp, st, &b.ctl->error, ERRB_TIMEOUT);
         cur = c2 ? (cur ^ 1) : cur;
     }
     cudaMemsetAsync(o.view_trk, 0, sizeof(long long) * (b.V + 1), st);
@@ -592,7 +592,7 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_fit<<<g, 256, 0, st>>>(b, w, o);
     const int tbits = bits_for((unsigned long long)(acc_cap > 0 ? acc_cap : 1));
     int cm = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], out_member_cap,
-                                  &b.ctl->n_out_members, b.rbits + tbits, temp, st);
+                                  &b.ctl->n_out_members, b.rbits + tbits, temp, st, &b.ctl->error, ERRB_TIMEOUT);
     k_members_out<<<g, 256, 0, st>>>(b, o, o.sort_k[cm]);
 }
 

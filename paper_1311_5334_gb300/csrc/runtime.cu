@@ -536,7 +536,7 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
         launch_canonical_keys(b, keys[0], vals[0], st);
         const int kb = b.vshift + bits_for((unsigned long long)std::max(V - 1, 0));
-        int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st);
+        int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st, &ctl->error, ERRB_TIMEOUT);
         u32 *sv = vals[c1], *cell_of = vals[c1 ^ 1];
         launch_canonical_order(b, keys[c1], sv, cell_of, cell_count, st);
         // cell list by counting sort: starts from the counts, then the counts
@@ -639,7 +639,7 @@ et_status BatchRT::settle(bool record) {
         if (s != ET_OK) return s;
         if (hctl.error & ERRB_OUT_OF_RANGE) return fail(ET_ERR_OUT_OF_RANGE, "a grain lies outside [0, extent)");
         if (hctl.error & ERRB_DUPLICATE) return fail(ET_ERR_DUPLICATE_GRAIN, "two grains share coordinates");
-        if (hctl.error & ERRB_TIMEOUT) return fail(ET_ERR_TIMEOUT, "device-side wait timed out in the merge");
+        if (hctl.error & ERRB_TIMEOUT) return fail(ET_ERR_TIMEOUT, "device-side wait timed out (merge barrier or sort look-back)");
         if (!(hctl.error & ERRB_OVF_MASK)) return ET_OK;
         if (attempt >= 6) return fail(ET_ERR_CAPACITY, "internal buffers kept overflowing");
         if (hctl.error & ERRB_OVF_CAND) {
