@@ -2,10 +2,9 @@
 //
 // Both run over a capacity-sized index range with an optional device-resident
 // element count, so that a fixed launch sequence (capturable in a CUDA graph)
-// can process data-dependent sizes.  The radix sort is the classic three-step
-// pass per 8-bit digit: per-tile digit histograms, one exclusive scan over
-// (digit, tile), and a stable scatter that ranks equal digits inside a tile by
-// warp match + popcount in index order.
+// can process data-dependent sizes.  The radix sort makes one histogram of all
+// digits up front and then one kernel per 8-bit digit, whose tiles find their
+// output offsets by a decoupled look-back (details at the kernels).
 #include <algorithm>
 
 #include "common.cuh"
