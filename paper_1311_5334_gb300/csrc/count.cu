@@ -634,7 +634,8 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
-    __shared__ unsigned long long cursor[TW][32];
+    __shared__ u32 cursor[TW][32];            // next slot, relative to the candidate's first
+    __shared__ unsigned long long mbase[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *__restrict__ members = w.members;
     const u64 tsize = ticket_size(nc);
@@ -652,12 +653,13 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
             sp[wib].put(lane, q);
-            cursor[wib][lane] = w.c_moff[c];
+            cursor[wib][lane] = 0;
+            mbase[wib][lane] = w.c_moff[c];
         }
         __syncwarp();
         u32 tests = 0;
         warp_items<false>(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
-            members[atomicAdd(&cursor[wib][own], 1ull)] = g.w;
+            members[mbase[wib][own] + atomicAdd(&cursor[wib][own], 1u)] = g.w;
         });
         __syncwarp();
     }
