@@ -330,6 +330,9 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[args.workload], "views_per_step": n_views,
                        "grains_per_step": int(offs[-1]),
                        "seeds_per_step": ref_stats["n_seeds"], "tube_tests_per_step": ref_stats["n_tests"],
+                       "tube_hits_per_step": ref_stats["n_hits"],
+                       "candidate_efficiency": (ref_stats["n_hits"] / ref_stats["n_tests"]
+                                                if ref_stats["n_tests"] else None),
                        "tracks_per_step": ref_stats["n_tracks"], "candidates_per_step": ref_stats["n_candidates"],
                        "candidate_members_per_step": ref_stats["n_members"],
                        "merge_rounds": ref_stats["merge_rounds"], "cell_units": list(ref_stats["cell"]),
