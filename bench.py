@@ -44,11 +44,11 @@ OPS_PER_TEST = 14
 # DRAM bytes one launch of the tube-count kernel (seed generation and tube
 # counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of that launch (one pass, the first timed step):
-#   batched  706.94 MB + 46.80 MB  (256 views, autotuned cells 74x506x506, both lists)
+#   batched  611.68 MB + 45.84 MB  (256 views, autotuned cells 74x621x506, both lists)
 # The kernel reads each view's grains and cell tables about once, so the bytes
 # follow the views and the cell shape rather than the seeds; workloads without
 # a capture of their own launch report null.
-TUBE_DRAM_BYTES = {"batched": 706.94e6 + 46.80e6}
+TUBE_DRAM_BYTES = {"batched": 611.68e6 + 45.84e6}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
@@ -269,7 +269,7 @@ def run_ours(args):
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
         tuned = {"cell": list(cell), "row_lists": batch.tuning["row_lists"], "ms_per_run": ms,
-                 "how": "et_batch_autotune: fastest of 8 cell shapes, each with x rows and with x+y rows"}
+                 "how": "et_batch_autotune: fastest of 11 cell shapes, each with x rows and with x+y rows"}
 
     def step():
         batch.load(xyz_d, offs, stream=stream)

@@ -167,7 +167,8 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
     const double s0 = std::cbrt(0.35 * vol / nmean);
     // (x, y, z) factors of s0; rows run along x, so x cells may be short
     static const double cand[][3] = {{0.22, 1.1, 1.1}, {0.33, 1.3, 1.3}, {0.16, 1.1, 1.1}, {0.27, 0.95, 0.95},
-                                     {0.22, 1.3, 1.3}, {0.33, 1.1, 1.1}, {0.5, 1.6, 1.3}, {1.0, 1.0, 1.0}};
+                                     {0.22, 1.3, 1.3}, {0.33, 1.1, 1.1}, {0.5, 1.6, 1.3}, {1.0, 1.0, 1.0},
+                                     {0.16, 1.22, 1.22}, {0.16, 1.35, 1.1}, {0.18, 1.6, 1.6}};
     const int ncand = (int)(sizeof cand / sizeof cand[0]);
     if (max_trials <= 0 || max_trials > ncand) max_trials = ncand;
     const et_tuning saved = tune;
