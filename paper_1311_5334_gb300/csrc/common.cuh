@@ -163,11 +163,10 @@ int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, 
                      cudaStream_t st, u32 *err, u32 err_bit);
 size_t scan_temp_bytes(long long n);
 // Exclusive prefix sum of n values; writes n + 1 outputs (the last = total).
-// If total_out != nullptr the total is also stored there.  In place allowed.
-void exclusive_scan_u64(const u64 *in, u64 *out, long long n, void *temp, u64 *total_out,
-                        cudaStream_t st);
+// In place allowed.
 void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaStream_t st);
-// Same over [0, min(*n_dev, n_cap)) when n_dev is not null.
+// Same for u64 over [0, min(*n_dev, n_cap)) when n_dev is not null; the total
+// is also stored in *total_out when total_out is not null.
 void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
                             u64 *total_out, cudaStream_t st);
 int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,

@@ -292,11 +292,6 @@ size_t scan_temp_bytes(long long n) {
     return (size_t)nb * sizeof(u64);
 }
 
-void exclusive_scan_u64(const u64 *in, u64 *out, long long n, void *temp, u64 *total_out,
-                        cudaStream_t st) {
-    scan_impl<u64>(in, out, n, nullptr, temp, total_out, st);
-}
-
 void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaStream_t st) {
     scan_impl<u32>(in, out, n, nullptr, temp, nullptr, st);
 }
