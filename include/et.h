@@ -111,7 +111,9 @@ typedef struct {
 typedef struct {
     int32_t cell[3];        /* cell-list edge per axis, coordinate units; 0: automatic
                                (s0 * (0.22, 1.1, 1.1), s0 the edge of a cube holding 0.35
-                               grains at the batch's mean density) */
+                               grains at the batch's mean density).  The batch's cell table
+                               (views x cells per view) must stay below 2^31 - 1 cells, else
+                               loading fails with ET_ERR_INVALID_ARG */
     int32_t block_seeds;    /* reserved */
     int32_t row_lists;      /* 1: one cell list, rows along x; 2: also a list with rows
                                along y, used by lines whose |w_y| > |w_x|; 0: automatic (2) */

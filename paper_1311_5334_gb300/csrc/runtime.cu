@@ -127,6 +127,10 @@ BatchRT::~BatchRT() {
         g->release(ctx);
 }
 
+// Cells of one batch's cell table (views x cells per view): the kernels index
+// it with 32-bit signed arithmetic.
+static constexpr double kMaxCells = 2147483647.0;
+
 void BatchRT::choose_cells() {
     for (int k = 0; k < 3; ++k) cs[k] = tune.cell[k];
     if (cs[0] <= 0 || cs[1] <= 0 || cs[2] <= 0) {
@@ -183,7 +187,7 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
         t.row_lists = 1 + (k & 1);
         tune = t;
         choose_cells();
-        if ((double)V * (double)std::max(ncell, ncelly) >= 4.0e9) continue;
+        if ((double)V * (double)std::max(ncell, ncelly) >= kMaxCells) continue;
         et_status s = reserve();
         if (s != ET_OK) {
             tune = saved;
@@ -420,8 +424,9 @@ et_status BatchRT::load(const int32_t *xyz, const int64_t *offsets, int nv, bool
     goff_h.assign(offsets, offsets + nv + 1);
     for (int k = 0; k < 3; ++k) cbits[k] = cb[k];
     choose_cells();
-    if ((double)V * (double)std::max(ncell, ncelly) >= 4.0e9)
-        return fail(ET_ERR_INVALID_ARG, "cell table too large");
+    if ((double)V * (double)std::max(ncell, ncelly) >= kMaxCells)
+        return fail(ET_ERR_INVALID_ARG, "cell table of %.3g cells too large (limit 2^31 - 1)",
+                    (double)V * (double)std::max(ncell, ncelly));
     estimate_caps();
     et_status s = reserve();
     if (s != ET_OK) return s;

@@ -318,6 +318,28 @@ def test_coordinates_at_the_limit(et, ctx, oracle_mod):
     assert_same(et, tracks, members, want)
 
 
+def test_cell_table_limit(et, ctx):
+    # the cell table is indexed with 32-bit signed arithmetic: a tuning that
+    # would make 2^31 cells (16384 x 16384 x 8 cells of 128 units) is refused
+    # on load, before any allocation, and an automatic grid still works
+    E = 1 << 21
+    xyz = np.array([[5, 5, 5], [300, 5, 5]], dtype=np.int32)
+    p = dict(extent=(E, E, 1024), seed_min=100, seed_max=400, tube_r=20, min_hits=2)
+    v = et.View.create(ctx, xyz, p)
+    try:
+        v.set_tuning((128, 128, 128), row_lists=1)
+        with pytest.raises(et.EtError) as e:
+            v.load_host(xyz)
+        assert e.value.status == et.INVALID_ARG
+        v.set_tuning((0, 0, 0), row_lists=0)
+        v.load_host(xyz)
+        v.find()
+        tracks, members = v.fetch()
+        assert len(tracks) == 1 and sorted(members.tolist()) == [0, 1]
+    finally:
+        v.close()
+
+
 def test_input_errors(et, ctx):
     with pytest.raises(et.EtError) as e:
         v = et.View.create(ctx, np.array([[1, 2, 3], [1000, 2, 3]]), _p())
