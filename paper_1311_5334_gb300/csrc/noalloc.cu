@@ -13,9 +13,12 @@
 // process exits.  In host code its name is only a stand-in: the device
 // address is obtained once per device with cudaGetSymbolAddress (on the first
 // call on that device, which should therefore happen before any stream
-// capture) and passed to the kernels.  Every call shares the array and leaves
-// its contents behind; calls whose work overlaps on the GPU race with each
-// other, so callers must order them (one stream, or events).
+// capture) and passed to the kernels.  The address is cached together with
+// the device's current CUDA context; after a device reset the context
+// differs, and the next call looks the address up again.  Every call shares
+// the array and leaves its contents behind; calls whose work overlaps on the
+// GPU race with each other, so callers must order them (one stream, or
+// events).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -121,8 +124,12 @@ __global__ void k_na_scatter(Batch b, const int *xyz, NaScratch s) {
 }
 
 // One thread per pair: the exact tube test over the conservative cell cover.
-// A pair with an index outside [0, n) or equal indices, and every pair when
-// a coordinate was out of range, gets -1.
+// A pair with an index outside [0, n) or equal indices, a pair whose two
+// grains coincide or lie seed_max or more apart on some axis, and every pair
+// when a coordinate was out of range, gets -1.  The separation bound keeps
+// every cross-product component an exact int32 (|d_e w_f| + |d_f w_e| <
+// (extent_e + extent_f) seed_max < 2^31, the parameter precondition) and the
+// squared norms within 64 bits, as for the seeds of the regular path.
 __global__ void k_na_tube(Batch b, const int *xyz, const int *pairs, long long n_pairs, int *counts,
                           NaScratch s) {
     const bool bad_view = *(volatile u32 *)s.flag != 0;
@@ -135,6 +142,11 @@ __global__ void k_na_tube(Batch b, const int *xyz, const int *pairs, long long n
         }
         const int3 a = make_int3(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]);
         const int3 d = make_int3(xyz[3 * j] - a.x, xyz[3 * j + 1] - a.y, xyz[3 * j + 2] - a.z);
+        if ((d.x == 0 && d.y == 0 && d.z == 0) || abs(d.x) >= b.smax || abs(d.y) >= b.smax ||
+            abs(d.z) >= b.smax) {
+            counts[k] = -1;
+            continue;
+        }
         const long long R = b.r2 * ((long long)d.x * d.x + (long long)d.y * d.y + (long long)d.z * d.z);
         int c = 0;
         const int4 *__restrict__ g = s.grains;
@@ -147,6 +159,28 @@ __global__ void k_na_tube(Batch b, const int *xyz, const int *pairs, long long n
 
 std::mutex g_na_mu;
 unsigned char *g_na_base[64] = {};
+void *g_na_ctx[64] = {};   // the CUDA context the cached address belongs to
+
+// The calling thread's current CUDA context (a driver handle), through the
+// runtime's driver entry point so that the library needs no -lcuda.
+void *current_context() {
+    typedef int (*GetCurrent)(void **);
+    static GetCurrent fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (GetCurrent)f;
+        cudaGetLastError();
+        looked = true;
+    }
+    void *c = nullptr;
+    if (fn && fn(&c) != 0) c = nullptr;
+    return c;
+}
 
 }  // namespace
 
@@ -172,11 +206,13 @@ extern "C" et_status et_tube_count_noalloc(const int32_t *d_xyz, int64_t n, cons
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> g(g_na_mu);
-        if (!g_na_base[dev]) {
+        void *cur = current_context();
+        if (!g_na_base[dev] || cur != g_na_ctx[dev]) {
             void *p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the scratch array");
             g_na_base[dev] = (unsigned char *)p;
+            g_na_ctx[dev] = current_context();
         }
         base = g_na_base[dev];
     }
@@ -188,6 +224,7 @@ extern "C" et_status et_tube_count_noalloc(const int32_t *d_xyz, int64_t n, cons
     for (int k = 0; k < 3; ++k) b.ext[k] = params->extent[k];
     b.r = params->tube_r;
     b.r2 = (long long)params->tube_r * params->tube_r;
+    b.smax = params->seed_max;
     const double vol = (double)b.ext[0] * b.ext[1] * b.ext[2];
     double sz = std::cbrt(vol / (double)std::max<int64_t>(n, 1));
     long long ncell = 0;
