@@ -51,7 +51,7 @@
 extern "C" {
 #endif
 
-#define ET_ABI_VERSION 2
+#define ET_ABI_VERSION 3
 
 typedef int32_t et_status;
 #define ET_OK                    0
@@ -160,6 +160,7 @@ typedef struct {
      * the tube-count kernel), 2 seeds + tube counts, 3 candidate keys + member
      * lists, 4 merge, 5 output (order, fit, members) */
     float stage_ms[6];
+    int64_t n_pair_tests;   /* seed-window tests the seed generator made (grain pairs examined) */
 } et_stats;
 
 typedef struct et_ctx et_ctx;
@@ -219,7 +220,9 @@ et_status et_track_fetch(et_view *view, et_track *tracks, int64_t cap, int64_t *
  * seed hypothesis, in no particular order (parity checks and diagnostics).
  * The view runs the path once more with a per-seed record buffer (no flag or
  * earlier setup needed).  Returns ET_ERR_CAPACITY with *n_seeds = required
- * size if cap is too small. */
+ * size if cap is too small.  Also accepts a batch (an et_view is a batch of
+ * one): seed_i / seed_j then index the batch's grains back to back, i.e.
+ * offsets[v] + the index within view v. */
 et_status et_view_seed_counts(et_view *view, int32_t *seed_i, int32_t *seed_j, int32_t *count,
                               int64_t cap, int64_t *n_seeds);
 
@@ -307,9 +310,11 @@ et_status et_server_destroy(et_server *s);
  * For each pair k (d_pairs[2k], d_pairs[2k+1]: indices into the view's grains)
  * it writes to d_counts[k] the number of grains of the view within tube_r of
  * the line through the two grains -- the same exact count et_view_seed_counts
- * reports for a seed -- or -1 for a pair with an index outside [0, n) or two
- * equal indices, and for every pair if a coordinate lies outside
- * [0, extent).  d_xyz (int32 [n][3]), d_pairs (int32 [n_pairs][2]) and d_counts
+ * reports for a seed -- or -1 for a pair with an index outside [0, n), two
+ * equal indices, two grains at the same coordinates, or grains seed_max or
+ * more apart along some axis (the bound under which the exact integer test
+ * cannot overflow; every seed of the window lies within it), and -1 for every
+ * pair if a coordinate lies outside [0, extent).  d_xyz (int32 [n][3]), d_pairs (int32 [n_pairs][2]) and d_counts
  * (int32 [n_pairs]) are DEVICE memory of the current device, owned by the
  * caller; the work is enqueued on `stream` (NULL = legacy default stream) and
  * the call returns without waiting.
@@ -318,7 +323,8 @@ et_status et_server_destroy(et_server *s);
  * array of about 3 MB (ET_NOALLOC_MAX_GRAINS grains, ET_NOALLOC_MAX_CELLS cells)
  * that every GPU which loads the library keeps until the process exits.  The
  * first call on a device looks up that array's device address; make it
- * before any stream capture.  All calls share the array, so calls whose work
+ * before any stream capture (the address is looked up again after a device
+ * reset has replaced the device's context).  All calls share the array, so calls whose work
  * overlaps on the GPU race: order them (one stream, or events).  Views larger
  * than ET_NOALLOC_MAX_GRAINS are rejected with ET_ERR_INVALID_ARG. */
 #define ET_NOALLOC_MAX_GRAINS 65536

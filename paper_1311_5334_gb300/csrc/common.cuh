@@ -46,6 +46,7 @@ struct Ctl {
     u64 ncl[2];         // merge: lengths of the undecided-candidate lists (ping-pong)
     u32 round_active[64];   // merge: participants of the first 64 rounds (diagnostics)
     u64 ticket[2];          // work tickets of the tube-count and member-list kernels
+    u64 n_pair_tests;       // seed-window tests of the seed generator
 };
 
 // Everything a kernel needs to know about the batch.  Passed by value.

@@ -210,9 +210,19 @@ __device__ __forceinline__ int4 grain_at(const Batch &b, u32 k) {
     return b.gc[k];
 }
 
-template <bool PACKED, class Hit>
+// Adds 1 to a shared-memory counter when p holds, without a branch.
+__device__ __forceinline__ void red_add_if(bool p, u32 *addr) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q red.shared.add.u32 [%1], 1;\n\t}" ::"r"((unsigned)p),
+                 "r"(a)
+                 : "memory");
+}
+
+// COUNT: in the dealt passes every grain inside the tube of line s adds 1 to
+// cnt[s] by a predicated reduction; otherwise hit(s, g) is called for it.
+template <bool PACKED, bool COUNT, class Hit>
 __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u32 &tests,
-                                           Hit &&hit) {
+                                           u32 *cnt, Hit &&hit) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_le = 0xffffffffu >> (31 - lane);
     const unsigned lane_lt = lane_le >> 1;
@@ -350,8 +360,15 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
             if (v1) g1 = grain_at<PACKED>(b, k1);
             const long long R0 = (long long)(((unsigned long long)(unsigned)q0.w << 32) | (unsigned)q0.z);
             const long long R1 = (long long)(((unsigned long long)(unsigned)q1.w << 32) | (unsigned)q1.z);
-            if (in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0)) hit(ow0, g0);
-            if (v1 && in_tube(g1, make_int3(p1.x, p1.y, p1.z), make_int3(p1.w, q1.x, q1.y), R1)) hit(ow1, g1);
+            const bool h0 = in_tube(g0, make_int3(p0.x, p0.y, p0.z), make_int3(p0.w, q0.x, q0.y), R0);
+            const bool h1 = v1 && in_tube(g1, make_int3(p1.x, p1.y, p1.z), make_int3(p1.w, q1.x, q1.y), R1);
+            if (COUNT) {
+                red_add_if(h0, &cnt[ow0]);
+                red_add_if(h1, &cnt[ow1]);
+            } else {
+                if (h0) hit(ow0, g0);
+                if (h1) hit(ow1, g1);
+            }
         }
         if (base < rtotal) {
             const bool st = n > 0 && rex >= base && rex < base + 32;
@@ -365,7 +382,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                 const int4 e0 = sp.i4(0, ow), e1 = sp.i4(1, ow);
                 const int4 g = grain_at<PACKED>(b, k);
                 const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
-                if (in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R)) hit(ow, g);
+                const bool h = in_tube(g, make_int3(e0.x, e0.y, e0.z), make_int3(e0.w, e1.x, e1.y), R);
+                if (COUNT) red_add_if(h, &cnt[ow]);
+                else if (h) hit(ow, g);
             }
         }
         __syncwarp();   // the table is rewritten by the next round
@@ -395,7 +414,9 @@ struct GenSm {
     int ofirst[SG];   // first row item of each origin (the group's total if none)
     int2 tbl[32];     // round's non-empty rows: first position minus pass position, owner origin
     uint2 rr[32];     // per lane: pass position and length of the lane's row in the round
+    int ov[SG];       // view of each origin
     int2 q[SQ];       // seeds waiting for the tube walk (lo, hi)
+    int qv[SQ];       // their views
 };
 
 struct GenState {
@@ -404,6 +425,7 @@ struct GenState {
     u32 rtotal = 0;   // grains of the current round
     u32 pbase = 0;    // next pass position in the round
     u32 cnt = 0;      // queued seeds
+    u32 pair_tests = 0;   // seed-window tests made by this lane (far below 2^32 in one launch)
 };
 
 // Takes the next SG origins; false when none is left.
@@ -430,6 +452,7 @@ __device__ __forceinline__ bool gen_group(const Batch &b, GenSm &sm, GenState &g
         sm.og[lane] = g;
         sm.oc[lane] = make_int4(cx0, cx1, cy0, cz0);
         sm.on[lane] = make_int2(ny, (int)((u32)v * (u32)b.ncell));
+        sm.ov[lane] = v;
     }
     int incl = nrows;
 #pragma unroll
@@ -505,7 +528,7 @@ __device__ __forceinline__ bool gen_pass(const Batch &b, GenSm &sm, GenState &gs
     const int bef = __popc(__ballot_sync(0xffffffffu, r.y > 0 && r.x < base));
     const u32 i = base + lane;
     bool hit = false;
-    int lo = 0, hi = 0;
+    int lo = 0, hi = 0, view = 0;
     if (i < gs.rtotal) {
         const int2 t = sm.tbl[bef + __popc(pm & lane_le) - 1];
         const int4 h = b.gc[i + (u32)t.x];
@@ -515,9 +538,15 @@ __device__ __forceinline__ bool gen_pass(const Batch &b, GenSm &sm, GenState &gs
         hit = h.w > g.w && d2 >= b.smin2 && d2 < b.smax2;
         lo = g.w;
         hi = h.w;
+        view = sm.ov[t.y];
+        ++gs.pair_tests;
     }
     const unsigned hm = __ballot_sync(0xffffffffu, hit);
-    if (hit) sm.q[gs.cnt + __popc(hm & lane_lt)] = make_int2(lo, hi);
+    if (hit) {
+        const int slot = gs.cnt + __popc(hm & lane_lt);
+        sm.q[slot] = make_int2(lo, hi);
+        sm.qv[slot] = view;
+    }
     gs.cnt += __popc(hm);
     gs.pbase = base + 32;
     __syncwarp();
@@ -540,25 +569,29 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         if (gs.cnt == 0) break;
         const u32 m = min(gs.cnt, 32u);
         const bool valid = lane < (int)m;
-        int lo = 0, hi = 0, n_items = 0;
+        int lo = 0, hi = 0, view = 0, n_items = 0;
         if (valid) {
             const int2 sd = gsm[wib].q[lane];
             lo = sd.x;
             hi = sd.y;
+            view = gsm[wib].qv[lane];
         }
         __syncwarp();
-        if (lane + 32 < (int)gs.cnt) gsm[wib].q[lane] = gsm[wib].q[lane + 32];
+        if (lane + 32 < (int)gs.cnt) {
+            gsm[wib].q[lane] = gsm[wib].q[lane + 32];
+            gsm[wib].qv[lane] = gsm[wib].qv[lane + 32];
+        }
         gs.cnt -= m;
         nseeds += m;
         if (valid) {
             SeedSm q;
-            n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
+            n_items = seed_setup(b, b.gr[lo], b.gr[hi], view, q);
             sp[wib].put(lane, q);
         }
         scount[wib][lane] = 0;
         __syncwarp();
-        warp_items<true>(b, sp[wib], tbl[wib], n_items, tests,
-                         [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
+        warp_items<true, true>(b, sp[wib], tbl[wib], n_items, tests, scount[wib],
+                               [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
         hits += count;
@@ -568,9 +601,10 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
             r0 = __shfl_sync(0xffffffffu, r0, 0);
             if (valid) {
                 const u64 s = r0 + lane;
-                if (s < w.rec_cap) {
-                    w.rec_lo[s] = b.gr[lo].w;
-                    w.rec_hi[s] = b.gr[hi].w;
+                if (s < w.rec_cap) {   // indices into the batch's grains back to back
+                    const int vbase = (int)b.goff[view];
+                    w.rec_lo[s] = vbase + b.gr[lo].w;
+                    w.rec_hi[s] = vbase + b.gr[hi].w;
                     w.rec_cnt[s] = (int)count;
                 } else {
                     atomicOr(&b.ctl->error, ERRB_OVF_RECORD);
@@ -598,8 +632,10 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         __syncwarp();
     }
     const u64 wtests = warp_sum_u64(tests), whits = warp_sum_u64(hits);
+    const u64 wpairs = warp_sum_u64(gs.pair_tests);
     if (lane == 0) {
         if (wtests) atomicAdd(&b.ctl->n_tests, wtests);
+        if (wpairs) atomicAdd(&b.ctl->n_pair_tests, wpairs);
         if (whits) atomicAdd(&b.ctl->n_hits, whits);
         if (nseeds) atomicAdd(&b.ctl->n_seeds, nseeds);
     }
@@ -658,7 +694,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
         }
         __syncwarp();
         u32 tests = 0;
-        warp_items<false>(b, sp[wib], tbl[wib], n_items, tests, [&](int own, int4 g) {
+        warp_items<false, false>(b, sp[wib], tbl[wib], n_items, tests, cursor[wib], [&](int own, int4 g) {
             members[mbase[wib][own] + atomicAdd(&cursor[wib][own], 1u)] = g.w;
         });
         __syncwarp();

@@ -768,6 +768,7 @@ void BatchRT::stats(et_stats *o) {
     o->n_members = (int64_t)hctl.n_members;
     o->n_tracks = (int64_t)hctl.n_acc;
     o->n_track_members = (int64_t)hctl.n_out_members;
+    o->n_pair_tests = (int64_t)hctl.n_pair_tests;
     o->merge_rounds = (int32_t)hctl.rounds;
     for (int k = 0; k < 3; ++k) o->cell[k] = cs[k];
     o->kernel_launches = count_kernels();

@@ -58,7 +58,7 @@ class Stats(C.Structure):
                 ("n_hits", C.c_int64), ("n_candidates", C.c_int64), ("n_members", C.c_int64),
                 ("n_tracks", C.c_int64), ("n_track_members", C.c_int64), ("merge_rounds", C.c_int32),
                 ("cell", C.c_int32 * 3), ("kernel_launches", C.c_int32), ("profiled", C.c_int32),
-                ("stage_ms", C.c_float * 6)]
+                ("stage_ms", C.c_float * 6), ("n_pair_tests", C.c_int64)]
 
     STAGES = ("cells", "seeds", "tube_count", "members", "merge", "output")
 
@@ -363,6 +363,18 @@ class Batch:
         _check(lib().et_batch_stats(self._h, C.byref(s)))
         return s.as_dict()
 
+    def seed_counts(self):
+        """All seeds (seed_i, seed_j, count) of the last run, unordered; for a
+        batch the indices run over all views' grains back to back."""
+        L = lib()
+        ns = C.c_int64()
+        st = L.et_view_seed_counts(self._h, None, None, None, 0, C.byref(ns))
+        if st not in (OK, CAPACITY):
+            _check(st)
+        a, b, c = (np.zeros(ns.value, dtype=np.int32) for _ in range(3))
+        _check(L.et_view_seed_counts(self._h, _ptr(a), _ptr(b), _ptr(c), ns.value, C.byref(ns)))
+        return a, b, c
+
     def close(self):
         if getattr(self, "_h", None):
             lib().et_batch_destroy(self._h)
@@ -411,17 +423,6 @@ class View(Batch):
     def fetch(self, out=None):
         """(tracks structured array, members int32); out: optional arrays to reuse."""
         return _fetch(lib().et_track_fetch, self._h, out=out)
-
-    def seed_counts(self):
-        """All seeds (seed_i, seed_j, count) of the last run, unordered."""
-        L = lib()
-        ns = C.c_int64()
-        st = L.et_view_seed_counts(self._h, None, None, None, 0, C.byref(ns))
-        if st not in (OK, CAPACITY):
-            _check(st)
-        a, b, c = (np.zeros(ns.value, dtype=np.int32) for _ in range(3))
-        _check(L.et_view_seed_counts(self._h, _ptr(a), _ptr(b), _ptr(c), ns.value, C.byref(ns)))
-        return a, b, c
 
 
 class Server:

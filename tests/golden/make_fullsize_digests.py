@@ -1,0 +1,88 @@
+"""Writes the expected full-size results of the batched workload (256 views of
+300x300x50 um, seed 3) and the stress workload (one 1000x1000x50 um view,
+seed 5) as digests: fullsize_batched_seed3.json and fullsize_stress_seed5.json
+beside this script.
+
+Every expected value comes from the CPU oracle (oracle/), which evaluates the
+definition of Section 2 and Fig. 4 of the paper: seeds in the distance window,
+exact tube counts over all grains, threshold, sequential greedy exclusive
+association.  Nothing here calls the CUDA library.
+
+  python tests/golden/make_fullsize_digests.py [batched|stress|all] [--threads T]
+
+Takes minutes on a multi-core host (the per-seed tube counts run on all cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+sys.path.insert(0, HERE)
+
+import fullsize  # noqa: E402
+from oracle import oracle as O  # noqa: E402
+from paper_1311_5334_gb300 import synth  # noqa: E402
+
+
+def view_record(v, p, threads):
+    o = O.Oracle(v.xyz, p["extent"], p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"])
+    try:
+        tr, (slo, shi, scnt) = o.find_tracks(nthreads=threads, keep_seeds=True)
+    finally:
+        o.close()
+    n_seeds, sd = fullsize.seed_digest(slo, shi, scnt)
+    return {
+        "n_grains": v.n,
+        "input_sha256": fullsize.input_digest(v.xyz),
+        "n_seeds": n_seeds,
+        "seed_hash": sd,
+        "n_hits": int(scnt.astype("int64").sum()),
+        "n_candidates": int(tr.n_cand),
+        "n_tracks": len(tr),
+        "n_track_members": int(tr.moff[-1]) if len(tr) else 0,
+        "tracks_sha256": fullsize.track_digest(tr.as_tuples()),
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("which", nargs="?", default="all", choices=["batched", "stress", "all"])
+    ap.add_argument("--threads", type=int, default=0)
+    a = ap.parse_args()
+    O.build()
+    if a.which in ("batched", "all"):
+        t0 = time.time()
+        views = synth.batched(n_views=256, seed=3)
+        p = synth.params(views[0].extent)
+        recs = []
+        for k, v in enumerate(views):
+            recs.append(view_record(v, p, a.threads))
+            print(f"batched view {k}: {v.n} grains, {recs[-1]['n_tracks']} tracks "
+                  f"({time.time() - t0:.0f} s)", flush=True)
+        out = {"workload": "batched: synth.batched(n_views=256, seed=3), synth.params",
+               "source": "oracle/oracle.c via oracle.Oracle.find_tracks(keep_seeds=True)",
+               "views": recs}
+        with open(os.path.join(HERE, "fullsize_batched_seed3.json"), "w") as f:
+            json.dump(out, f, indent=0)
+    if a.which in ("stress", "all"):
+        t0 = time.time()
+        v = synth.stress()
+        p = synth.params(v.extent)
+        rec = view_record(v, p, a.threads)
+        print(f"stress: {v.n} grains, {rec['n_seeds']} seeds, {rec['n_tracks']} tracks "
+              f"({time.time() - t0:.0f} s)", flush=True)
+        out = {"workload": "stress: synth.stress(seed=5), synth.params",
+               "source": "oracle/oracle.c via oracle.Oracle.find_tracks(keep_seeds=True)",
+               "view": rec}
+        with open(os.path.join(HERE, "fullsize_stress_seed5.json"), "w") as f:
+            json.dump(out, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -45,7 +45,7 @@ def test_binding_signatures_cover_the_header():
 
 def test_abi_version_and_status_strings(libet):
     libet.et_abi_version.restype = C.c_int32
-    assert libet.et_abi_version() == 2
+    assert libet.et_abi_version() == 3
     libet.et_status_string.restype = C.c_char_p
     libet.et_status_string.argtypes = [C.c_int32]
     assert libet.et_status_string(-3) == b"duplicate grain"
@@ -55,7 +55,7 @@ def test_track_layout_matches_header():
     from paper_1311_5334_gb300 import et
     assert et.TRACK_DTYPE.itemsize == 64
     assert C.sizeof(et.Params) == 48
-    assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4 + 4 * 2 + 4 * 6
+    assert C.sizeof(et.Stats) == 8 * 8 + 4 * 4 + 4 * 2 + 4 * 6 + 8
     assert C.sizeof(et.FrameParams) == 4 * 4 + 4 * 3 + 4 * 3 + 4 + 4
     assert C.sizeof(et.FramesStats) == 8 * 4 + 4 * 4
 
