@@ -41,6 +41,10 @@ METRIC = "views/s"
 # One tube-membership test: 3 IADD (offset), 6 IMUL/IMAD (int32 cross product),
 # 3 IMAD.WIDE (64-bit squared norm), 2 for the 64-bit compare.
 OPS_PER_TEST = 14
+# One seed-window test of the seed generator: 3 IADD (offset), 3 IMAD.WIDE
+# (squared distance); the two compares with the window and the rank test are
+# not counted.
+OPS_PER_PAIR_TEST = 6
 # DRAM bytes one launch of the tube-count kernel (seed generation and tube
 # counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of that launch (one pass, the first timed step):
@@ -153,7 +157,7 @@ WORKLOADS = {
 }
 
 
-def make_workload(name="batched"):
+def make_workload(name="batched", n_batched=256):
     if name == "dense":
         views = [synth.dense()]
     elif name == "pr1":
@@ -161,7 +165,7 @@ def make_workload(name="batched"):
     elif name == "stress":
         views = [synth.stress()]
     else:
-        views = synth.batched(n_views=256, seed=3)
+        views = synth.batched(n_views=256, seed=3)[:n_batched]
     xyz, offs = synth.concat(views)
     return views, xyz, offs
 
@@ -173,8 +177,9 @@ def workload_params(views, args=None):
     return synth.params(views[0].extent, flags=args.flags, cut=tuple(int(c) for c in args.cut.split(",")))
 
 
-def oracle_views_per_s(views, budget_s, start=0, args=None):
-    """Times the oracle on views[start:] until budget_s of wall time is used."""
+def oracle_views_per_s(views, budget_s, start=0, args=None, threads=0):
+    """Times the oracle on views[start:] until budget_s of wall time is used
+    (threads: OpenMP threads of the counting, 0 = all cores)."""
     from oracle import oracle as O
     O.build()
     p = workload_params(views, args)
@@ -186,7 +191,7 @@ def oracle_views_per_s(views, budget_s, start=0, args=None):
         t0 = time.perf_counter()
         with O.Oracle(v.xyz, v.extent, p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"],
                       flags=p["flags"], cut=p["cut"]) as o:
-            tr = o.find_tracks()
+            tr = o.find_tracks(nthreads=threads)
         t_used += time.perf_counter() - t0
         done += 1
         seeds += tr.n_seeds
@@ -237,6 +242,10 @@ def run_ours(args):
     from paper_1311_5334_gb300 import et
 
     ws, rank, local = dist_env()
+    # the served sweep's views are drawn by spawned processes before any CUDA call
+    served_pool = None
+    if not args.no_extra and args.workload == "batched":
+        served_pool = served_views_pool(args.served_views, seed=4)
     torch.cuda.set_device(local)
     dist = None
     if ws > 1:
@@ -248,7 +257,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    views, xyz_h, offs = make_workload(args.workload)
+    views, xyz_h, offs = make_workload(args.workload, args.views)
     n_views = len(views)
     params = workload_params(views, args)
     # a dedicated stream: the legacy default stream (handle 0) would mean
@@ -268,8 +277,10 @@ def run_ours(args):
     batch.load(xyz_d, offs, stream=stream)
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
-        tuned = {"cell": list(cell), "row_lists": batch.tuning["row_lists"], "ms_per_run": ms,
-                 "how": "et_batch_autotune: fastest of 11 cell shapes, each with x rows and with x+y rows"}
+        tuned = {"cell": list(cell), "row_lists": batch.tuning["row_lists"],
+                 "ticket_origins": batch.tuning["ticket_origins"], "ms_per_run": ms,
+                 "how": "et_batch_autotune: fastest of 11 cell shapes, each with x rows and with x+y rows, "
+                        "then 1, 2 or 4 seed origins per work ticket for that shape"}
 
     def step():
         batch.load(xyz_d, offs, stream=stream)
@@ -311,8 +322,10 @@ def run_ours(args):
     # the nominal peak and, beside it, the device's measured integer issue rates
     tube_avg_ms = float(np.mean(tube_ms))
     int_rates = ctx.int_throughput()
-    ops = OPS_PER_TEST * ref_stats["n_tests"]
+    ops_tube = OPS_PER_TEST * ref_stats["n_tests"]
+    ops = ops_tube + OPS_PER_PAIR_TEST * ref_stats["n_pair_tests"]
     achieved = ops / (tube_avg_ms / 1e3) / 1e12
+    achieved_tube = ops_tube / (tube_avg_ms / 1e3) / 1e12
     peak = info["sm_count"] * 128 * 2070e6 / 1e12
     stage_ms = ref_stats["stage_ms"]
 
@@ -327,10 +340,13 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "views_per_step": n_views,
+            "config": {"workload": (WORKLOADS[args.workload] if args.workload != "batched" or n_views == 256
+                                    else f"first {n_views} views of " + WORKLOADS[args.workload]),
+                       "views_per_step": n_views,
                        "grains_per_step": int(offs[-1]),
                        "seeds_per_step": ref_stats["n_seeds"], "tube_tests_per_step": ref_stats["n_tests"],
                        "tube_hits_per_step": ref_stats["n_hits"],
+                       "seed_window_tests_per_step": ref_stats["n_pair_tests"],
                        "candidate_efficiency": (ref_stats["n_hits"] / ref_stats["n_tests"]
                                                 if ref_stats["n_tests"] else None),
                        "tracks_per_step": ref_stats["n_tracks"], "candidates_per_step": ref_stats["n_candidates"],
@@ -347,11 +363,13 @@ def run_ours(args):
             "wall_s": wall,
             "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak,
+                         "frac_tube_tests_only": achieved_tube / peak,
                          "traffic": TUBE_DRAM_BYTES.get(args.workload),
-                         "basis": f"{OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests / "
-                                  f"{tube_avg_ms:.3f} ms (in-graph CUDA events; the kernel also generates "
-                                  f"the seeds); peak = "
-                                  f"{info['sm_count']} SMs x 128 lanes x 2070 MHz",
+                         "basis": f"({OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests + "
+                                  f"{OPS_PER_PAIR_TEST} per seed-window test x {ref_stats['n_pair_tests']} "
+                                  f"window tests of the seed generator) / {tube_avg_ms:.3f} ms (in-graph "
+                                  f"CUDA events of the one kernel that generates the seeds and counts their "
+                                  f"tubes); peak = {info['sm_count']} SMs x 128 lanes x 2070 MHz",
                          "measured_int_tops": {k: v / 1e12 for k, v in int_rates.items()},
                          "frac_of_measured_mix": achieved / (int_rates["mix"] / 1e12),
                          "measured_how": "et_probe_int_throughput: xor+add (alu), a*a+z (mad) and both (mix) "
@@ -361,9 +379,7 @@ def run_ours(args):
             "gpu_launches": int(ref_stats["kernel_launches"]) * args.steps,
             "clocks": clk}
     if not args.no_extra and args.workload == "batched":
-        rate, nv = args.served_rate, args.served_views
-        line["served"] = served_run(ctx, params, views, rate, nv)
-        line["served"]["pool"] = f"arrivals cycle over the {n_views} batched views; 20 GB budget"
+        line["served"] = served_sweep(ctx, params, served_pool)
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra:
         budget = float(os.environ.get("ET_CPU_BASELINE_S", "15"))
@@ -372,6 +388,12 @@ def run_ours(args):
                                 "sample": f"views {names[0]}..{names[-1]} ({d} of {n_views}) of the step, "
                                           f"{t:.1f} s; counting parallel over all cores (OpenMP), "
                                           "merge and fit single-threaded"}
+        # one host thread: the paper's CPU comparison basis (Section 3, Table 2)
+        d1, s1, t1, names1 = oracle_views_per_s(views, budget / 2, args=args, threads=1)
+        line["cpu_baseline_1thread"] = {"value": d1 / t1, "unit": "views/s", "cores": 1, "kind": "oracle",
+                                        "seeds_per_s": s1 / t1,
+                                        "sample": f"views {names1[0]}..{names1[-1]} ({d1} of {n_views}) "
+                                                  f"of the step, {t1:.1f} s, one thread"}
     batch.close()
     ctx.close()
     if rank == 0:
@@ -381,8 +403,38 @@ def run_ours(args):
     return 0
 
 
+SERVED_RATES = (100, 200, 500, 1000, 2000, 5000)
+
+
+def _served_view(arg):
+    seed, i, n_fog = arg
+    return synth.batched_view(seed, i, n_fog).xyz
+
+
+def served_views_pool(n_views=10000, seed=4):
+    """The served workload's views: n_views distinct views with the batched
+    size law (seed 4), drawn in parallel by spawned worker processes (no CUDA
+    state is inherited)."""
+    import multiprocessing as mp
+    sizes = synth.batched_sizes(n_views, seed)
+    args = [(seed, i, int(nf)) for i, nf in enumerate(sizes)]
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        return pool.map(_served_view, args, chunksize=64)
+
+
+def served_sweep(ctx, params, pool, budget_bytes=20 << 30):
+    """The served configuration: len(pool) views arriving as a Poisson
+    process at each rate of SERVED_RATES, under a device-memory budget."""
+    out = {"views_per_rate": len(pool), "budget_bytes": budget_bytes,
+           "pool": f"{len(pool)} distinct views, batched size law (lognormal, median 10k), seed 4", "rates": []}
+    for rate in SERVED_RATES:
+        out["rates"].append(served_run(ctx, params, pool, rate, len(pool), budget_bytes=budget_bytes))
+    return out
+
+
 def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batch=256, seed=4):
     """Poisson arrivals at `rate` views/s through et_server_submit / et_server_poll.
+    pool: views (objects with .xyz) or int32 (n, 3) arrays, cycled.
 
     Latency of a view = result ready - its scheduled arrival (CLOCK_MONOTONIC on
     both sides), so a producer that falls behind does not hide queueing."""
@@ -399,7 +451,8 @@ def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batc
                 wait = int(sched[i]) - time.monotonic_ns()
                 if wait > 0:
                     time.sleep(wait / 1e9)
-                while srv.submit(pool[i % len(pool)].xyz, tag=i) == et.BUSY:
+                v = pool[i % len(pool)]
+                while srv.submit(getattr(v, "xyz", v), tag=i) == et.BUSY:
                     busy[0] += 1
                     time.sleep(1e-4)
 
@@ -411,10 +464,13 @@ def served_run(ctx, params, pool, rate, n_views, budget_bytes=20 << 30, max_batc
                     raise RuntimeError(f"served view {r.tag} failed with status {r.status}")
                 done[int(r.tag)] = int(r.t_done_ns)
         th.join()
+        sst = srv.stats()
     lat = np.array([(done[i] - sched[i]) / 1e6 for i in range(n_views)])
     span = (max(done.values()) - t0) / 1e9
     return {"rate_per_s": rate, "views": n_views, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "views_per_s": n_views / span, "busy_retries": busy[0]}
+            "p99_ms": float(np.percentile(lat, 99)), "views_per_s": n_views / span, "busy_retries": busy[0],
+            "micro_batches": sst["batches"], "peak_device_bytes": sst["peak_device_bytes"],
+            "budget_bytes": budget_bytes}
 
 
 def pinned_array(n, dtype):
@@ -717,10 +773,12 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="time only the device-resident step (no plain/e2e/cpu baseline); for profilers")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batched")
+    ap.add_argument("--views", type=int, default=256,
+                    help="batched workload: time only its first N views (smaller profiling captures)")
     ap.add_argument("--cell", default="", help="cell edges x,y,z in coordinate units (default: automatic)")
     ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
-    ap.add_argument("--served-rate", type=float, default=1000.0, help="Poisson rate of the served run (views/s)")
-    ap.add_argument("--served-views", type=int, default=3000, help="views in the served run")
+    ap.add_argument("--served-views", type=int, default=10000,
+                    help="distinct views of the served sweep (one run per rate of 100..5000 views/s)")
     ap.add_argument("--flags", type=int, default=0,
                     help="et_params.flags: 1 single-pass association, 2 angle cut (tracking workloads)")
     ap.add_argument("--cut", default="0,0,0", help="angle cut base,slope,tan_max (with --flags 2)")
@@ -746,15 +804,13 @@ def run_served_sweep(args):
     20 GB device-memory budget.  One JSON line per rate."""
     import torch
     from paper_1311_5334_gb300 import et
+    pool = served_views_pool(args.served_views, seed=4)
     torch.cuda.set_device(0)
-    pool = synth.batched(n_views=512, seed=4)
-    params = synth.params(pool[0].extent)
+    params = synth.params((30000, 30000, 5000))
     with et.Context(0) as ctx:
-        for rate in (100, 200, 500, 1000, 2000, 5000):
-            n = min(args.served_views if args.served_views != 3000 else 10000, 10000)
-            r = served_run(ctx, params, pool, rate, n)
-            r.update({"metric": "served view latency", "pool": "512 distinct views (seed 4) cycled",
-                      "budget_bytes": 20 << 30})
+        for rate in SERVED_RATES:
+            r = served_run(ctx, params, pool, rate, len(pool))
+            r.update({"metric": "served view latency", "pool": f"{len(pool)} distinct views (seed 4)"})
             print(json.dumps(r), flush=True)
     return 0
 

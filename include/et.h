@@ -114,13 +114,20 @@ typedef struct {
                                grains at the batch's mean density).  The batch's cell table
                                (views x cells per view) must stay below 2^31 - 1 cells, else
                                loading fails with ET_ERR_INVALID_ARG */
-    int32_t block_seeds;    /* reserved */
+    int32_t ticket_origins; /* origins per work ticket of the seed generator (a warp takes
+                               this many consecutive grains as line origins at a time):
+                               1, 2 or 4; 0: automatic (2) */
     int32_t row_lists;      /* 1: one cell list, rows along x; 2: also a list with rows
                                along y, used by lines whose |w_y| > |w_x|; 0: automatic (2) */
     int32_t assoc_window;   /* candidates per window of the exclusive association (the
                                rounds run window by window in candidate order); 0: automatic
                                (at least 2^18, at most 128 windows) */
-    int32_t reserved[2];
+    int32_t wait_polls;     /* 0: default.  Otherwise every bounded device-side wait (the
+                               association's grid barrier, the sorts' look-back) gives up
+                               after this many polls and the run fails with ET_ERR_TIMEOUT.
+                               Small values make a wait run out on purpose (tests of the
+                               timeout path); the next run with 0 is unaffected */
+    int32_t reserved;
 } et_tuning;
 
 /* One reconstructed track.  seed_i / seed_j are indices into the caller's grain
@@ -240,12 +247,13 @@ et_status et_batch_create(et_ctx *ctx, const et_params *params, et_batch **out);
 et_status et_batch_load(et_batch *b, const int32_t *xyz, const int64_t *offsets, int32_t n_views,
                         int32_t on_device, void *stream);
 et_status et_batch_set_tuning(et_batch *b, const et_tuning *tuning);
-/* Picks the cell-list shape for the loaded batch by timing the whole path on
- * it: up to max_trials candidate shapes derived from the batch's mean grain
+/* Picks the tuning for the loaded batch by timing the whole path on it: up to
+ * max_trials candidate cell shapes derived from the batch's mean grain
  * density (mostly anisotropic, cells along the x rows kept short), each with
- * one cell list and with both lists, two runs each, CUDA-event timed;
- * the fastest is kept as the batch's tuning and returned in *chosen (may be
- * NULL), its time per run in *best_ms (may be NULL).
+ * one cell list and with both lists, then 1, 2 and 4 origins per work ticket
+ * for the fastest shape (unless ticket_origins was set); two runs each,
+ * CUDA-event timed.  The fastest is kept as the batch's tuning and returned in
+ * *chosen (may be NULL), its time per run in *best_ms (may be NULL).
  * Synchronous.  Results never depend on the choice, only the speed does. */
 et_status et_batch_autotune(et_batch *b, void *stream, int32_t max_trials, et_tuning *chosen, float *best_ms);
 /* Enqueues the path for all loaded views.  use_graph != 0 captures the launch
@@ -268,9 +276,14 @@ et_status et_batch_destroy(et_batch *b);
 /* ------------------------------------------------------------------ server */
 
 /* A served loop: views are submitted one by one as a scanning microscope
- * emits them, admitted while their device memory fits `mem_budget_bytes`,
- * grouped into micro-batches by a worker thread and processed on the device;
- * per-view results stay on the device until polled. */
+ * emits them, grouped into micro-batches by a worker thread and processed on
+ * the device; per-view results are kept until polled.  Two micro-batches
+ * alternate (one runs while the next is staged).  mem_budget_bytes bounds the
+ * device memory both micro-batches hold together at any time: a micro-batch is
+ * admitted only while its planned buffers plus the other one's fit, and a
+ * micro-batch whose buffers would have to grow past what the other leaves
+ * (after a candidate overflow) fails its views with ET_ERR_OOM.  Host staging
+ * memory is not counted. */
 typedef struct {
     uint64_t tag;            /* caller's tag from et_server_submit */
     et_status status;
@@ -282,10 +295,22 @@ typedef struct {
     int64_t t_done_ns;
 } et_result;
 
+/* Counters of a server. */
+typedef struct {
+    uint64_t budget_bytes;
+    uint64_t device_bytes;       /* device memory its micro-batches hold now */
+    uint64_t peak_device_bytes;  /* the most they held together at any time */
+    int64_t views_done;          /* views whose results were produced */
+    int64_t batches;             /* micro-batches run */
+    int64_t busy_rejections;     /* submits answered with ET_ERR_BUSY */
+    int64_t pending;             /* views queued, not yet admitted */
+} et_server_stats;
+
 et_status et_server_create(et_ctx *ctx, const et_params *params, uint64_t mem_budget_bytes,
                            int32_t max_batch_views, et_server **out);
 /* Copies the view's grains (host memory) and queues it.  ET_ERR_BUSY if the
- * pending queue is full. */
+ * pending queue is full (back-pressure: retry later) or if the view alone
+ * needs more device memory than the budget. */
 et_status et_server_submit(et_server *s, const int32_t *xyz, int64_t n, uint64_t tag);
 /* Returns up to `max` finished views (oldest first), waiting up to timeout_us
  * microseconds for at least one.  Each result's tracks may be copied with
@@ -296,6 +321,10 @@ et_status et_server_poll(et_server *s, et_result *out, int32_t max, int32_t *n_d
 et_status et_server_fetch(et_server *s, uint64_t tag, et_track *tracks, int64_t cap,
                           int64_t *n_tracks, int32_t *members, int64_t member_cap,
                           int64_t *n_members);
+/* Pending-queue length at which et_server_submit answers ET_ERR_BUSY
+ * (default 2^20 views; at least 1). */
+et_status et_server_set_max_pending(et_server *s, int64_t max_pending);
+et_status et_server_get_stats(et_server *s, et_server_stats *out);
 et_status et_server_destroy(et_server *s);
 
 /* ------------------------------------------------------------------ no allocation */

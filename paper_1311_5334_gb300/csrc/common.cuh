@@ -59,6 +59,8 @@ struct Batch {
     int smin, smax, r, H;
     long long smin2, smax2, r2;
     unsigned flags;          // ET_FLAG_* variants
+    long long spin_limit;    // polls before a bounded device wait gives up (0: defaults)
+    int gen_origins;         // origins per work ticket of the seed generator (1, 2 or 4)
     int cut_base, cut_slope, cut_tmax;   // angle cut (ET_FLAG_ANGLE_CUT)
     // cell grid (identical for all views)
     int cs[3];           // cell edge per axis
@@ -158,10 +160,12 @@ __device__ __forceinline__ bool input_failed(const Ctl *ctl) {
 size_t radix_temp_bytes(long long n);
 // Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key.
 // Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
-// (k0, v0), 1 if in (k1, v1).  A pass whose tile waits past its limit for a
-// predecessor sets err_bit in *err (the result is then invalid).
+// (k0, v0), 1 if in (k1, v1).  A pass whose tile polls a predecessor more
+// than spin_limit times (0: the default limit, about half a second) sets
+// err_bit in *err; the result is then invalid, but every write stays inside
+// [0, n).
 int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp,
-                     cudaStream_t st, u32 *err, u32 err_bit);
+                     cudaStream_t st, u32 *err, u32 err_bit, long long spin_limit = 0);
 size_t scan_temp_bytes(long long n);
 // Exclusive prefix sum of n values; writes n + 1 outputs (the last = total).
 // In place allowed.
@@ -171,7 +175,7 @@ void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaSt
 void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
                             u64 *total_out, cudaStream_t st);
 int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,
-                         void *temp, cudaStream_t st, u32 *err, u32 err_bit);
+                         void *temp, cudaStream_t st, u32 *err, u32 err_bit, long long spin_limit = 0);
 // Kernel launches of one radix sort on bits bits (histogram, bases, passes).
 inline int radix_sort_launches(int bits) { return bits > 0 ? 2 + (bits + 7) / 8 : 0; }
 

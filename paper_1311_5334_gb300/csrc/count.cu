@@ -395,7 +395,8 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
 //
 // Seeds (Section 2) are the pairs of grains of one view with
 // seed_min^2 <= |g_b - g_a|^2 < seed_max^2, each pair once (a of lower
-// canonical rank).  A warp takes SG origins a at a time (consecutive in the
+// canonical rank).  A warp takes b.gen_origins origins a at a time (1, 2 or 4,
+// a tuning choice; consecutive in the
 // x-row cell order, one work ticket).  The cell rows that can hold their
 // partners -- the (y, z) cells within seed_max - 1 of a, each an x run from
 // a's cell to the largest admissible dx -- are dealt to the lanes in rounds
@@ -404,7 +405,7 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
 // in shared memory; the tube walk takes them 32 at a time.  So seeds are
 // walked in the order origin, row, x, and concurrently running warps work on
 // nearby origins: no seed list is written to memory.
-constexpr int SG = 2;          // origins per work ticket (small: even a one-view batch fills the grid)
+constexpr int SG = 4;          // most origins per work ticket (b.gen_origins: 1, 2 or 4)
 constexpr int SQ = 64;         // seed queue: < 32 waiting + one pass
 
 struct GenSm {
@@ -428,17 +429,17 @@ struct GenState {
     u32 pair_tests = 0;   // seed-window tests made by this lane (far below 2^32 in one launch)
 };
 
-// Takes the next SG origins; false when none is left.
+// Takes the next b.gen_origins origins; false when none is left.
 __device__ __forceinline__ bool gen_group(const Batch &b, GenSm &sm, GenState &gs) {
     const int lane = threadIdx.x & 31;
     u64 g0 = 0;
-    if (lane == 0) g0 = atomicAdd(&b.ctl->ticket[0], (u64)SG);
+    if (lane == 0) g0 = atomicAdd(&b.ctl->ticket[0], (u64)b.gen_origins);
     g0 = __shfl_sync(0xffffffffu, g0, 0);
     const u64 N = (u64)b.N;
     if (g0 >= N) return false;
     const int reach = b.smax - 1;   // >= 0: seed_max >= 1
     int nrows = 0;
-    if (lane < SG && g0 + lane < N) {
+    if (lane < b.gen_origins && g0 + lane < N) {
         const int4 g = b.gc[g0 + lane];
         const int v = view_of(b.goff, b.V, g.w);
         const int cx0 = g.x / b.cs[0];

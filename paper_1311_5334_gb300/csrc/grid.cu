@@ -37,6 +37,9 @@ __global__ void k_canonical_keys(Batch b, u64 *keys, u32 *vals) {
 
 __global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u32 *cell_of,
                                   u32 *cell_count) {
+    // a coordinate out of range is reported as such; a timed-out sort leaves
+    // invalid indices: either way nothing after this point may run
+    if (input_failed(b.ctl)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
         const int v = view_of(b.goff, b.V, p);
@@ -60,6 +63,7 @@ __global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u32
 // slot of its cell (cursor zeroed before the launch).
 __global__ void k_cell_scatter(Batch b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int4 *gc,
                                u64 *gp) {
+    if (input_failed(b.ctl)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
         const u32 c = cell_of[p];
@@ -72,6 +76,7 @@ __global__ void k_cell_scatter(Batch b, const u32 *cell_of, const u32 *cell_star
 
 // Cells of the second cell list (rows along y) for the canonical order.
 __global__ void k_y_cells(Batch b, u32 *cell_of, u32 *cell_count) {
+    if (input_failed(b.ctl)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
         const int v = view_of(b.goff, b.V, p);

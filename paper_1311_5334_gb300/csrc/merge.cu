@@ -52,8 +52,10 @@ constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;  // x ~128 ns slee
 __device__ __forceinline__ u32 ld_cg_u32(const u32 *p) { return __ldcg(p); }
 
 // Grid-wide barrier for a cooperative launch.  Returns false if it timed out
-// (or another block recorded a timeout): the caller must then return.
-__device__ bool grid_barrier(Ctl *ctl, unsigned nblocks) {
+// (polls beyond the limit; 0: the default of about 2 s) or another block
+// recorded a timeout: the caller must then return.
+__device__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long long limit) {
+    const unsigned long long lim = limit > 0 ? (unsigned long long)limit : BARRIER_SPIN_LIMIT;
     __syncthreads();
     if (threadIdx.x == 0) {
         volatile u32 *gen = &ctl->bar_gen;
@@ -67,7 +69,7 @@ __device__ bool grid_barrier(Ctl *ctl, unsigned nblocks) {
         } else {
             unsigned long long spins = 0;
             while (*gen == g) {
-                if (++spins > BARRIER_SPIN_LIMIT || (*(volatile u32 *)&ctl->error & ERRB_TIMEOUT)) {
+                if (++spins > lim || (*(volatile u32 *)&ctl->error & ERRB_TIMEOUT)) {
                     atomicOr(&ctl->error, ERRB_TIMEOUT);
                     break;
                 }
@@ -148,14 +150,14 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             ++my_active;
         }
         if (lane == 0 && my_active) atomicAdd(&ctl->active[round & 1], my_active);
-        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
         const u32 active = ld_cg_u32(&ctl->active[round & 1]);
         if (blockIdx.x == 0 && threadIdx.x == 0 && round < 64) ctl->round_active[round] = active;
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->active[(round + 1) & 1] = 0;
         if (active == 0) {   // the window is decided (uniform: every block read the same count)
             ++round;
             // the next window's first round counts into the counter just reset
-            if (!grid_barrier(ctl, gridDim.x)) return;
+            if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
             break;
         }
         // ---- phase 2: accept ready candidates, carry the others to the next round
@@ -253,7 +255,7 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             if (lane < nkeep) next[pos + lane] = keep[wib][lane];
             __syncwarp();
         }
-        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
     }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
@@ -342,6 +344,7 @@ __global__ void k_collect(Batch b, Work w, Out o) {
 
 // After the key sort: second key = view (stable sort keeps key order).
 __global__ void k_view_keys(Batch b, Work w, u64 *k, const u32 *v) {
+    if (input_failed(b.ctl)) return;   // a timed-out sort leaves invalid indices
     const u64 na = b.ctl->n_acc;
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < na; i += stride)
@@ -350,6 +353,7 @@ __global__ void k_view_keys(Batch b, Work w, u64 *k, const u32 *v) {
 
 // Sorted accepted list -> per-track view, nhits (for the member scan) and per-view counts.
 __global__ void k_track_meta(Batch b, Work w, Out o, const u32 *sorted_c) {
+    if (input_failed(b.ctl)) return;
     const u64 na = b.ctl->n_acc;
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < na; t += stride) {
@@ -415,6 +419,7 @@ __device__ void jacobi3f(float A[3][3], float V[3][3]) {
 // One warp per accepted track: exact integer moments about the lo seed grain,
 // FP32 principal axis, member projections; member keys for the final sort.
 __global__ void k_fit(Batch b, Work w, Out o) {
+    if (input_failed(b.ctl)) return;
     const u64 na = b.ctl->n_acc;
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -472,8 +477,10 @@ __global__ void k_fit(Batch b, Work w, Out o) {
         bool flip = dot < 0.0f;
         if (dot == 0.0f) flip = (u[0] != 0.0f) ? u[0] < 0.0f : ((u[1] != 0.0f) ? u[1] < 0.0f : u[2] < 0.0f);
         if (flip) { u[0] = -u[0]; u[1] = -u[1]; u[2] = -u[2]; }
-        // centroid relative to the lo grain; projections use exact integer
-        // offsets so their rounding scales with the track, not the view
+        // centroid relative to the lo grain.  A member's offset from the
+        // centroid, times n, is the exact integer n d - S1 (d its offset from
+        // the lo grain), so a projection's rounding scales with the
+        // projection itself, not with the view or the track length
         const float fn = (float)n;
         const float ca[3] = {(float)s1[0] / fn, (float)s1[1] / fn, (float)s1[2] / fn};
         const float cen[3] = {(float)ga.x + ca[0], (float)ga.y + ca[1], (float)ga.z + ca[2]};
@@ -484,8 +491,10 @@ __global__ void k_fit(Batch b, Work w, Out o) {
                 const int g = w.members[m];
                 if (w.owner[g] == c) {
                     const int4 p = b.gr[g];
-                    const float tt = ((float)(p.x - ga.x) - ca[0]) * u[0] + ((float)(p.y - ga.y) - ca[1]) * u[1] +
-                                     ((float)(p.z - ga.z) - ca[2]) * u[2];
+                    const long long ex = n * (long long)(p.x - ga.x) - s1[0];
+                    const long long ey = n * (long long)(p.y - ga.y) - s1[1];
+                    const long long ez = n * (long long)(p.z - ga.z) - s1[2];
+                    const float tt = ((float)ex * u[0] + (float)ey * u[1] + (float)ez * u[2]) / fn;
                     tmin = fminf(tmin, tt);
                     tmax = fmaxf(tmax, tt);
                 }
@@ -515,6 +524,7 @@ __global__ void k_fit(Batch b, Work w, Out o) {
 }
 
 __global__ void k_members_out(Batch b, Out o, const u64 *sorted_k) {
+    if (input_failed(b.ctl)) return;
     const u64 nm = b.ctl->n_out_members;
     const u64 stride = (u64)gridDim.x * blockDim.x;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nm; i += stride)
@@ -559,7 +569,8 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
 const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st) {
     k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
     const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
-                                         &b.ctl->n_cand, 3 * b.rbits, temp, st, &b.ctl->error, ERRB_TIMEOUT);
+                                         &b.ctl->n_cand, 3 * b.rbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
+                                         b.spin_limit);
     return o.sort_v[cur];
 }
 
@@ -578,11 +589,12 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_collect<<<g, 256, 0, st>>>(b, w, o);
     u64 *na = &b.ctl->n_acc;
     int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 3 * b.rbits,
-                                   temp, st, &b.ctl->error, ERRB_TIMEOUT);
+                                   temp, st, &b.ctl->error, ERRB_TIMEOUT, b.spin_limit);
     if (b.V > 1) {
         k_view_keys<<<g, 256, 0, st>>>(b, w, o.sort_k[cur], o.sort_v[cur]);
         int c2 = radix_sort_pairs_dev(o.sort_k[cur], o.sort_v[cur], o.sort_k[cur ^ 1], o.sort_v[cur ^ 1], acc_cap,
-                                      na, bits_for((unsigned long long)(b.V - 1)), temp, st, &b.ctl->error, ERRB_TIMEOUT);
+                                      na, bits_for((unsigned long long)(b.V - 1)), temp, st, &b.ctl->error, ERRB_TIMEOUT,
+                                      b.spin_limit);
         cur = c2 ? (cur ^ 1) : cur;
     }
     cudaMemsetAsync(o.view_trk, 0, sizeof(long long) * (b.V + 1), st);
@@ -592,7 +604,8 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_fit<<<g, 256, 0, st>>>(b, w, o);
     const int tbits = bits_for((unsigned long long)(acc_cap > 0 ? acc_cap : 1));
     int cm = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], out_member_cap,
-                                  &b.ctl->n_out_members, b.rbits + tbits, temp, st, &b.ctl->error, ERRB_TIMEOUT);
+                                  &b.ctl->n_out_members, b.rbits + tbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
+                                  b.spin_limit);
     k_members_out<<<g, 256, 0, st>>>(b, o, o.sort_k[cm]);
 }
 

@@ -162,7 +162,9 @@ void BatchRT::choose_cells() {
 }
 
 // Autotuner: time the whole path for candidate cell shapes around the
-// density-based default s0 (about 0.35 grains per cell) and keep the fastest.
+// density-based default s0 (about 0.35 grains per cell), each with one and
+// with both cell lists, then the seed generator's work-ticket size (origins
+// per ticket) for the fastest shape, and keep the fastest combination.
 et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, float *best_ms) {
     if (!loaded) return fail(ET_ERR_NOT_READY, "no grains loaded");
     if (!st) st = ctx->stream;
@@ -180,44 +182,63 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
     profile = true;
     float best = 3.0e38f;
     et_tuning best_t = tune;
-    for (int k = 0; k < 2 * max_trials; ++k) {   // every shape with one and with both cell lists
-        et_tuning t = saved;
-        for (int a = 0; a < 3; ++a)
-            t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k / 2][a])));
-        t.row_lists = 1 + (k & 1);
+    // best of two timed runs of the path under tuning t (a negative time: skipped)
+    auto trial = [&](const et_tuning &t, float &ms_out) -> et_status {
+        ms_out = -1.0f;
         tune = t;
         choose_cells();
-        if ((double)V * (double)std::max(ncell, ncelly) >= kMaxCells) continue;
+        if ((double)V * (double)std::max(ncell, ncelly) >= kMaxCells) return ET_OK;
         et_status s = reserve();
-        if (s != ET_OK) {
-            tune = saved;
-            profile = saved_prof;
-            return s;
-        }
+        if (s != ET_OK) return s;
         float t_best = 3.0e38f;
         for (int rep = 0; rep < 2; ++rep) {
             s = enqueue(st, false);
-            if (s != ET_OK) {
-                tune = saved;
-                profile = saved_prof;
-                return s;
-            }
+            if (s != ET_OK) return s;
             cudaEventRecord(done, st);
             run_stream = st;
             ran = true;
             profiled_run = true;
             s = settle(false);
+            if (s != ET_OK) return s;
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev[0], ev[NSTAGE]) == cudaSuccess) t_best = std::min(t_best, ms);
+        }
+        ms_out = t_best;
+        return ET_OK;
+    };
+    for (int k = 0; k < 2 * max_trials; ++k) {   // every shape with one and with both cell lists
+        et_tuning t = saved;
+        for (int a = 0; a < 3; ++a)
+            t.cell[a] = std::max(16, std::min(p.extent[a], (int)std::lround(s0 * cand[k / 2][a])));
+        t.row_lists = 1 + (k & 1);
+        float ms = 0;
+        et_status s = trial(t, ms);
+        if (s != ET_OK) {
+            tune = saved;
+            profile = saved_prof;
+            return s;
+        }
+        if (ms >= 0.0f && ms < best) {
+            best = ms;
+            best_t = t;
+        }
+    }
+    if (saved.ticket_origins == 0) {   // origins per work ticket, for the fastest shape
+        const et_tuning shape = best_t;
+        for (int o : {1, 2, 4}) {
+            et_tuning t = shape;
+            t.ticket_origins = o;
+            float ms = 0;
+            et_status s = trial(t, ms);
             if (s != ET_OK) {
                 tune = saved;
                 profile = saved_prof;
                 return s;
             }
-            float ms = 0;
-            if (cudaEventElapsedTime(&ms, ev[0], ev[NSTAGE]) == cudaSuccess) t_best = std::min(t_best, ms);
-        }
-        if (t_best < best) {
-            best = t_best;
-            best_t = t;
+            if (ms >= 0.0f && ms < best) {
+                best = ms;
+                best_t = t;
+            }
         }
     }
     profile = saved_prof;
@@ -236,137 +257,230 @@ void BatchRT::estimate_caps() {
     const double shell = 4.0 / 3.0 * M_PI *
                          (std::pow((double)p.seed_max, 3) - std::pow((double)p.seed_min, 3));
     const double frac = std::min(1.0, shell / vol);
-    double s = 0;
-    for (int v = 0; v < V; ++v) {
-        double n = (double)(goff_h[v + 1] - goff_h[v]);
-        s += 0.5 * n * n * frac;
-    }
+    const double s = 0.5 * sum_n2 * frac;
     const u64 seeds = (u64)(1.3 * s) + 4096;   // seeds are not stored: they size the candidates
     want_cand = std::max(want_cand, std::max<u64>(65536, seeds / 16));
     want_members = std::max(want_members, want_cand * 24);
 }
 
-et_status BatchRT::reserve() {
-    // small: control block, goff, per-view track offsets
-    {
-        Carver cv;
-        cv.take<Ctl>(1);
-        cv.take<long long>(V + 1);
-        cv.take<long long>(V + 1);
-        if (!g_small.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "control block");
-        Carver c2{0, g_small.base};
-        ctl = c2.take<Ctl>(1);
-        goff = c2.take<long long>(V + 1);
-        view_trk = c2.take<long long>(V + 1);
-    }
+// Device arrays of one batch, carved out of eight groups (one allocation
+// each).  Carving with a null base only measures.
+struct DevPtrs {
+    Ctl *ctl = nullptr;
+    long long *goff = nullptr, *view_trk = nullptr;
+    int *xyz_in = nullptr;
+    u64 *keys[2] = {nullptr, nullptr};
+    u32 *vals[2] = {nullptr, nullptr};
+    int4 *gr = nullptr, *gc = nullptr, *gcy = nullptr;
+    u64 *gp = nullptr, *gpy = nullptr;
+    u64 *best[2] = {nullptr, nullptr};
+    int *owner = nullptr;
+    u32 *cell_count = nullptr, *cell_start = nullptr, *cell_count_y = nullptr, *cell_start_y = nullptr;
+    int *c_lo = nullptr, *c_hi = nullptr;
+    u32 *c_cnt = nullptr, *c_nfree = nullptr;
+    u64 *c_key = nullptr, *c_moff = nullptr;
+    unsigned char *c_state = nullptr;
+    int *clist[2] = {nullptr, nullptr};
+    int *members = nullptr;
+    int *acc = nullptr, *trk_view = nullptr, *out_members = nullptr;
+    u64 *sort_k[2] = {nullptr, nullptr};
+    u32 *sort_v[2] = {nullptr, nullptr};
+    u64 *trk_moff = nullptr;
+    et_track *tracks = nullptr;
+    int *rec_lo = nullptr, *rec_hi = nullptr, *rec_cnt = nullptr;
+    void *temp = nullptr;
+};
+
+// Carves group k (0 small, 1 grains, 2 cells, 3 candidates, 4 members,
+// 5 outputs, 6 seed records, 7 temporary) out of c; returns its size.
+size_t BatchRT::lay_group(int k, char *base, DevPtrs &P) const {
+    Carver c{0, base};
     const size_t n = (size_t)std::max<long long>(N, 1);
-    {
-        Carver cv;
-        auto lay = [&](Carver &c) {
-            xyz_in = c.take<int>(3 * n);
-            keys[0] = c.take<u64>(n);
-            keys[1] = c.take<u64>(n);
-            vals[0] = c.take<u32>(n);
-            vals[1] = c.take<u32>(n);
-            gr = c.take<int4>(n);
-            // the two cell orders back to back (the y-row list at offset n), so a
-            // walk addresses either through one array
-            gc = c.take<int4>(2 * n);
-            gcy = gc ? gc + n : nullptr;
-            gp = c.take<u64>(2 * n);
-            gpy = gp ? gp + n : nullptr;
-            best[0] = c.take<u64>(n);
-            best[1] = c.take<u64>(n);
-            owner = c.take<int>(n);
-        };
-        lay(cv);
-        if (!g_grain.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "grain buffers (%zu bytes)", cv.off);
-        Carver c2{0, g_grain.base};
-        lay(c2);
-    }
     const size_t cells = (size_t)V * (size_t)ncell, cellsy = (size_t)V * (size_t)ncelly;
-    {
-        auto lay = [&](Carver &c) {
-            cell_count = c.take<u32>(cells);
-            cell_start = c.take<u32>(cells + 1);
-            cell_count_y = c.take<u32>(cellsy);
-            cell_start_y = c.take<u32>(cellsy + 1);
-        };
-        Carver cv;
-        lay(cv);
-        if (!g_cells.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "cell tables (%zu bytes)", cv.off);
-        Carver c2{0, g_cells.base};
-        lay(c2);
-    }
-    {
+    switch (k) {
+    case 0:   // control block, goff, per-view track offsets
+        P.ctl = c.take<Ctl>(1);
+        P.goff = c.take<long long>(V + 1);
+        P.view_trk = c.take<long long>(V + 1);
+        break;
+    case 1:
+        P.xyz_in = c.take<int>(3 * n);
+        P.keys[0] = c.take<u64>(n);
+        P.keys[1] = c.take<u64>(n);
+        P.vals[0] = c.take<u32>(n);
+        P.vals[1] = c.take<u32>(n);
+        P.gr = c.take<int4>(n);
+        // the two cell orders back to back (the y-row list at offset n), so a
+        // walk addresses either through one array
+        P.gc = c.take<int4>(2 * n);
+        P.gcy = P.gc ? P.gc + n : nullptr;
+        P.gp = c.take<u64>(2 * n);
+        P.gpy = P.gp ? P.gp + n : nullptr;
+        P.best[0] = c.take<u64>(n);
+        P.best[1] = c.take<u64>(n);
+        P.owner = c.take<int>(n);
+        break;
+    case 2:
+        P.cell_count = c.take<u32>(cells);
+        P.cell_start = c.take<u32>(cells + 1);
+        P.cell_count_y = c.take<u32>(cellsy);
+        P.cell_start_y = c.take<u32>(cellsy + 1);
+        break;
+    case 3: {
         const size_t cc = want_cand;
-        auto lay = [&](Carver &c) {
-            c_lo = c.take<int>(cc);
-            c_hi = c.take<int>(cc);
-            c_cnt = c.take<u32>(cc);
-            c_key = c.take<u64>(cc);
-            c_moff = c.take<u64>(cc + 1);
-            c_state = c.take<unsigned char>(cc);
-            c_nfree = c.take<u32>(cc);
-            clist[0] = c.take<int>(cc);
-            clist[1] = c.take<int>(cc);
-        };
-        Carver cv;
-        lay(cv);
-        if (!g_cand.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "candidates (%zu bytes)", cv.off);
-        Carver c2{0, g_cand.base};
-        lay(c2);
-        cap_cand = cc;
+        P.c_lo = c.take<int>(cc);
+        P.c_hi = c.take<int>(cc);
+        P.c_cnt = c.take<u32>(cc);
+        P.c_key = c.take<u64>(cc);
+        P.c_moff = c.take<u64>(cc + 1);
+        P.c_state = c.take<unsigned char>(cc);
+        P.c_nfree = c.take<u32>(cc);
+        P.clist[0] = c.take<int>(cc);
+        P.clist[1] = c.take<int>(cc);
+        break;
     }
-    {
-        size_t need = want_members * sizeof(int);
-        if (!g_members.reserve(ctx, align_up(need, 256))) return fail(ET_ERR_OOM, "members (%zu bytes)", need);
-        members = (int *)g_members.base;
-        cap_members = g_members.bytes / sizeof(int);
+    case 4:
+        P.members = c.take<int>(want_members);
+        break;
+    case 5: {
+        const size_t cc = want_cand, sk = std::max<size_t>(cc, n);
+        P.acc = c.take<int>(cc);
+        P.sort_k[0] = c.take<u64>(sk);
+        P.sort_k[1] = c.take<u64>(sk);
+        P.sort_v[0] = c.take<u32>(sk);
+        P.sort_v[1] = c.take<u32>(sk);
+        P.trk_view = c.take<int>(cc);
+        P.trk_moff = c.take<u64>(cc + 1);
+        P.tracks = c.take<et_track>(cc);
+        P.out_members = c.take<int>(n);
+        break;
     }
-    {
-        const size_t cc = cap_cand, sk = std::max<size_t>(cc, n);
-        auto lay = [&](Carver &c) {
-            acc = c.take<int>(cc);
-            sort_k[0] = c.take<u64>(sk);
-            sort_k[1] = c.take<u64>(sk);
-            sort_v[0] = c.take<u32>(sk);
-            sort_v[1] = c.take<u32>(sk);
-            trk_view = c.take<int>(cc);
-            trk_moff = c.take<u64>(cc + 1);
-            tracks = c.take<et_track>(cc);
-            out_members = c.take<int>(n);
-        };
-        Carver cv;
-        lay(cv);
-        if (!g_out.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "outputs (%zu bytes)", cv.off);
-        Carver c2{0, g_out.base};
-        lay(c2);
-    }
-    if (want_rec) {
-        Carver cv;
-        cv.take<int>(want_rec);
-        cv.take<int>(want_rec);
-        cv.take<int>(want_rec);
-        if (!g_rec.reserve(ctx, cv.off)) return fail(ET_ERR_OOM, "seed records (%zu bytes)", cv.off);
-        Carver c2{0, g_rec.base};
-        rec_lo = c2.take<int>(want_rec);
-        rec_hi = c2.take<int>(want_rec);
-        rec_cnt = c2.take<int>(want_rec);
-        cap_rec = want_rec;
-    }
-    {
+    case 6:
+        if (want_rec) {
+            P.rec_lo = c.take<int>(want_rec);
+            P.rec_hi = c.take<int>(want_rec);
+            P.rec_cnt = c.take<int>(want_rec);
+        }
+        break;
+    default: {
         size_t t = 0;
         t = std::max(t, radix_temp_bytes((long long)n));
-        t = std::max(t, radix_temp_bytes((long long)std::max<size_t>(cap_cand, n)));
+        t = std::max(t, radix_temp_bytes((long long)std::max<size_t>(want_cand, n)));
         t = std::max(t, scan_temp_bytes((long long)std::max(cells, cellsy) + 1));
         t = std::max(t, scan_temp_bytes((long long)n + 1));
-        t = std::max(t, scan_temp_bytes((long long)cap_cand + 1));
+        t = std::max(t, scan_temp_bytes((long long)want_cand + 1));
         t = std::max(t, scan_temp_bytes((long long)V + 1));
-        if (!g_temp.reserve(ctx, align_up(t, 256))) return fail(ET_ERR_OOM, "temp (%zu bytes)", t);
-        temp = g_temp.base;
+        P.temp = c.take<char>(t);
+        break;
     }
+    }
+    return c.off;
+}
+
+Group *BatchRT::group(int k) {
+    Group *g[NGROUP] = {&g_small, &g_grain, &g_cells, &g_cand, &g_members, &g_out, &g_rec, &g_temp};
+    return g[k];
+}
+
+void BatchRT::plan_groups(size_t sizes[NGROUP]) const {
+    DevPtrs P;
+    for (int k = 0; k < NGROUP; ++k) sizes[k] = lay_group(k, nullptr, P);
+}
+
+size_t BatchRT::held_bytes() const {
+    size_t t = 0;
+    for (const Group *g : {&g_small, &g_grain, &g_cells, &g_cand, &g_members, &g_out, &g_rec, &g_temp}) t += g->bytes;
+    return t;
+}
+
+size_t BatchRT::footprint_with(const size_t sizes[NGROUP]) const {
+    const Group *g[NGROUP] = {&g_small, &g_grain, &g_cells, &g_cand, &g_members, &g_out, &g_rec, &g_temp};
+    size_t t = 0;
+    for (int k = 0; k < NGROUP; ++k) t += std::max(g[k]->bytes, sizes[k]);
+    return t;
+}
+
+void BatchRT::release_groups() {
+    for (int k = 0; k < NGROUP; ++k) group(k)->release(ctx);
+}
+
+et_status BatchRT::reserve() {
+    size_t sizes[NGROUP];
+    plan_groups(sizes);
+    if (byte_limit && footprint_with(sizes) > byte_limit)
+        return fail(ET_ERR_OOM, "device memory of %zu bytes would exceed the limit of %zu bytes",
+                    footprint_with(sizes), byte_limit);
+    static const char *what[NGROUP] = {"control block", "grain buffers", "cell tables", "candidates",
+                                       "members", "outputs", "seed records", "temp"};
+    DevPtrs P;
+    for (int k = 0; k < NGROUP; ++k) {
+        Group *g = group(k);
+        if (sizes[k] == 0) continue;
+        if (!g->reserve(ctx, sizes[k])) return fail(ET_ERR_OOM, "%s (%zu bytes)", what[k], sizes[k]);
+        lay_group(k, g->base, P);
+    }
+    ctl = P.ctl;
+    goff = P.goff;
+    view_trk = P.view_trk;
+    xyz_in = P.xyz_in;
+    keys[0] = P.keys[0];
+    keys[1] = P.keys[1];
+    vals[0] = P.vals[0];
+    vals[1] = P.vals[1];
+    gr = P.gr;
+    gc = P.gc;
+    gcy = P.gcy;
+    gp = P.gp;
+    gpy = P.gpy;
+    best[0] = P.best[0];
+    best[1] = P.best[1];
+    owner = P.owner;
+    cell_count = P.cell_count;
+    cell_start = P.cell_start;
+    cell_count_y = P.cell_count_y;
+    cell_start_y = P.cell_start_y;
+    c_lo = P.c_lo;
+    c_hi = P.c_hi;
+    c_cnt = P.c_cnt;
+    c_key = P.c_key;
+    c_moff = P.c_moff;
+    c_state = P.c_state;
+    c_nfree = P.c_nfree;
+    clist[0] = P.clist[0];
+    clist[1] = P.clist[1];
+    cap_cand = want_cand;
+    members = P.members;
+    cap_members = g_members.bytes / sizeof(int);
+    acc = P.acc;
+    sort_k[0] = P.sort_k[0];
+    sort_k[1] = P.sort_k[1];
+    sort_v[0] = P.sort_v[0];
+    sort_v[1] = P.sort_v[1];
+    trk_view = P.trk_view;
+    trk_moff = P.trk_moff;
+    tracks = P.tracks;
+    out_members = P.out_members;
+    if (want_rec) {
+        rec_lo = P.rec_lo;
+        rec_hi = P.rec_hi;
+        rec_cnt = P.rec_cnt;
+        cap_rec = want_rec;
+    }
+    temp = g_temp.base;
     return ET_OK;
+}
+
+// Sizes of the device groups a batch of the given shape would hold, without
+// allocating (the served loop's admission).
+void BatchRT::plan_shape(int nv, long long n, long long mx, double s2, size_t sizes[NGROUP]) {
+    V = nv;
+    N = n;
+    maxN = mx;
+    sum_n2 = s2;
+    want_cand = want_members = want_rec = 0;
+    choose_cells();
+    estimate_caps();
+    plan_groups(sizes);
 }
 
 unsigned long long BatchRT::layout_generation() const {
@@ -397,6 +511,9 @@ unsigned long long BatchRT::graph_signature() const {
     mix(cap_cand);
     mix(cap_members);
     mix(cap_rec);
+    mix((unsigned long long)tune.wait_polls);
+    mix((unsigned long long)tune.ticket_origins);
+    mix((unsigned long long)tune.assoc_window);
     return h;
 }
 
@@ -422,6 +539,8 @@ et_status BatchRT::load(const int32_t *xyz, const int64_t *offsets, int nv, bool
     N = total;
     maxN = mx;
     goff_h.assign(offsets, offsets + nv + 1);
+    sum_n2 = 0;
+    for (int v = 0; v < nv; ++v) sum_n2 += (double)(offsets[v + 1] - offsets[v]) * (double)(offsets[v + 1] - offsets[v]);
     for (int k = 0; k < 3; ++k) cbits[k] = cb[k];
     choose_cells();
     if ((double)V * (double)std::max(ncell, ncelly) >= kMaxCells)
@@ -461,6 +580,8 @@ Batch BatchRT::dev_batch() const {
     b.smax2 = (long long)p.seed_max * p.seed_max;
     b.r2 = (long long)p.tube_r * p.tube_r;
     b.flags = p.flags;
+    b.spin_limit = tune.wait_polls > 0 ? (long long)tune.wait_polls : 0;
+    b.gen_origins = tune.ticket_origins > 0 ? tune.ticket_origins : 2;
     const bool cut = (p.flags & ET_FLAG_ANGLE_CUT) != 0;
     b.cut_base = cut ? p.cut_base : 0;
     b.cut_slope = cut ? p.cut_slope : 0;
@@ -542,7 +663,8 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
         launch_canonical_keys(b, keys[0], vals[0], st);
         const int kb = b.vshift + bits_for((unsigned long long)std::max(V - 1, 0));
-        int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st, &ctl->error, ERRB_TIMEOUT);
+        int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st, &ctl->error, ERRB_TIMEOUT,
+                                  b.spin_limit);
         u32 *sv = vals[c1], *cell_of = vals[c1 ^ 1];
         launch_canonical_order(b, keys[c1], sv, cell_of, cell_count, st);
         // cell list by counting sort: starts from the counts, then the counts
@@ -906,6 +1028,9 @@ et_status et_batch_set_tuning(et_batch *b, const et_tuning *t) {
     for (int k = 0; k < 3; ++k)
         if (t->cell[k] < 0) return fail(ET_ERR_INVALID_ARG, "cell[%d] < 0", k);
     if (t->assoc_window < 0) return fail(ET_ERR_INVALID_ARG, "assoc_window < 0");
+    if (t->wait_polls < 0) return fail(ET_ERR_INVALID_ARG, "wait_polls < 0");
+    if (t->ticket_origins != 0 && t->ticket_origins != 1 && t->ticket_origins != 2 && t->ticket_origins != 4)
+        return fail(ET_ERR_INVALID_ARG, "ticket_origins = %d: 0, 1, 2 or 4", t->ticket_origins);
     b->tune = *t;
     b->loaded = false;   // the cell grid changes: reload required
     return ET_OK;

@@ -48,14 +48,18 @@ struct Group {
     void release(Ctx *ctx);
 };
 
+struct DevPtrs;
+
 // A batch of views sharing one et_params (a view is a batch of one).
 struct BatchRT {
+    static constexpr int NGROUP = 8;
     Ctx *ctx;
     et_params p;
     et_tuning tune;
     // shape
     int V = 0;
     long long N = 0, maxN = 0;
+    double sum_n2 = 0;   // sum over views of (grains)^2: sizes the candidate buffers
     std::vector<long long> goff_h;
     int cs[3] = {1, 1, 1}, nc[3] = {1, 1, 1}, cbits[3] = {0, 0, 0};
     long long ncell = 1;
@@ -66,6 +70,9 @@ struct BatchRT {
     u64 want_cand = 0, want_members = 0, want_rec = 0;
     // granted capacities
     u64 cap_cand = 0, cap_members = 0, cap_rec = 0;
+    // device bytes the groups may hold together after a reserve (0: no limit);
+    // a reserve beyond it fails with ET_ERR_OOM
+    size_t byte_limit = 0;
     // device memory
     Group g_small, g_grain, g_cells, g_cand, g_members, g_out, g_rec, g_temp;
     Ctl *ctl = nullptr;
@@ -112,6 +119,13 @@ struct BatchRT {
     void choose_cells();
     et_status autotune(cudaStream_t st, int max_trials, et_tuning *chosen, float *best_ms);
     void estimate_caps();
+    size_t lay_group(int k, char *base, DevPtrs &P) const;
+    Group *group(int k);
+    void plan_groups(size_t sizes[NGROUP]) const;
+    size_t held_bytes() const;
+    size_t footprint_with(const size_t sizes[NGROUP]) const;
+    void release_groups();
+    void plan_shape(int nv, long long n, long long mx, double s2, size_t sizes[NGROUP]);
     et_status reserve();
     unsigned long long layout_generation() const;
     unsigned long long graph_signature() const;

@@ -182,7 +182,7 @@ __global__ void k_rs_bases(u32 *gbase, int npass) {
 
 __global__ void __launch_bounds__(RS_T) k_rs_pass(const u64 *kin, const u32 *vin, u64 *kout, u32 *vout,
                                                   long long n_cap, const u64 *n_dev, int pass, RsTemp tp,
-                                                  u32 *err, u32 err_bit) {
+                                                  u32 *err, u32 err_bit, long long spin_limit) {
     __shared__ u32 s_tile;
     __shared__ u32 cnt[256];
     __shared__ u32 base_off[256];
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(RS_T) k_rs_pass(const u64 *kin, const u32 *vin
             while (u >= 0) {
                 const unsigned long long sv = *((volatile unsigned long long *)(tp.status + (size_t)u * 256 + t));
                 if ((sv >> 56) != (unsigned long long)(pass + 1) || (sv & (RS_AGG | RS_INC)) == 0) {
-                    if (++spins > RS_SPIN_LIMIT) {
+                    if (++spins > spin_limit) {
                         if (err) atomicOr(err, err_bit);
                         break;
                     }
@@ -308,7 +308,8 @@ size_t radix_temp_bytes(long long n) {
 }
 
 int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,
-                         void *temp, cudaStream_t st, u32 *err, u32 err_bit) {
+                         void *temp, cudaStream_t st, u32 *err, u32 err_bit, long long spin_limit) {
+    if (spin_limit <= 0) spin_limit = RS_SPIN_LIMIT;
     const long long ntiles = (n_cap + RS_TILE - 1) / RS_TILE;
     const int npass = (bits + 7) / 8;
     if (ntiles == 0 || npass == 0) return 0;
@@ -324,15 +325,15 @@ int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, co
     for (int p = 0; p < npass; ++p) {
         u64 *ki = cur ? k1 : k0, *ko = cur ? k0 : k1;
         u32 *vi = cur ? v1 : v0, *vo = cur ? v0 : v1;
-        k_rs_pass<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, vi, ko, vo, n_cap, n_dev, p, tp, err, err_bit);
+        k_rs_pass<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, vi, ko, vo, n_cap, n_dev, p, tp, err, err_bit, spin_limit);
         cur ^= 1;
     }
     return cur;
 }
 
 int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp, cudaStream_t st,
-                     u32 *err, u32 err_bit) {
-    return radix_sort_pairs_dev(k0, v0, k1, v1, n, nullptr, bits, temp, st, err, err_bit);
+                     u32 *err, u32 err_bit, long long spin_limit) {
+    return radix_sort_pairs_dev(k0, v0, k1, v1, n, nullptr, bits, temp, st, err, err_bit, spin_limit);
 }
 
 }  // namespace et

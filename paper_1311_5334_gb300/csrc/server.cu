@@ -2,13 +2,24 @@
 //
 // Views arrive one at a time, as a scanning microscope emits them (Section 3:
 // the stage delivers views at up to 5 Hz per microscope).  A worker thread
-// groups the views waiting in the queue into a micro-batch whose estimated
-// device memory fits the budget, runs the batched path on it and keeps the
-// per-view results until the caller polls them.  While one micro-batch runs,
-// new arrivals accumulate, so the batch size adapts to the arrival rate.  Two
-// micro-batches alternate: the next is staged and enqueued behind the running
-// one before the running one's results are collected, so the device does not
-// idle while the host gathers views and splits results.
+// groups the views waiting in the queue into a micro-batch, runs the batched
+// path on it and keeps the per-view results until the caller polls them.
+// While one micro-batch runs, new arrivals accumulate, so the batch size
+// adapts to the arrival rate.  Two micro-batches alternate: the next is
+// staged and enqueued behind the running one before the running one's
+// results are collected, so the device does not idle while the host gathers
+// views and splits results.
+//
+// Memory budget.  The two slots' batches hold device buffers that only grow
+// (a slot keeps its high-water buffers for the next micro-batch).  A
+// micro-batch is admitted only if the bytes its slot will hold -- per buffer
+// group the larger of what it holds and what the views need, planned with the
+// batch's own sizing code -- plus the bytes the other slot holds stay within
+// the budget.  When even the oldest view does not fit, the worker first waits
+// for the other slot's run to end, then frees the idle slot's buffers.  A
+// batch whose buffers must grow after a run (candidate overflow) may grow only
+// within what the other slot leaves; beyond that its views fail with
+// ET_ERR_OOM.
 #include "runtime.h"
 
 #include <chrono>
@@ -27,16 +38,6 @@ static int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(
                std::chrono::steady_clock::now().time_since_epoch())
         .count();
-}
-
-// Device bytes a view of n grains needs inside a batch (same formulas as the
-// batch's own sizing; seeds are not stored, they size the candidates).
-static uint64_t view_bytes(const et_params &p, int64_t n) {
-    const double vol = (double)p.extent[0] * p.extent[1] * p.extent[2];
-    const double shell = 4.0 / 3.0 * M_PI * (std::pow((double)p.seed_max, 3) - std::pow((double)p.seed_min, 3));
-    const double seeds = 1.3 * 0.5 * (double)n * (double)n * std::min(1.0, shell / vol) + 4096;
-    const double cand = std::max(65536.0 / 64, seeds / 16);
-    return (uint64_t)(n * 160.0 + cand * (48.0 + 24 * 4.0) + (1 << 20));
 }
 
 struct Pending {
@@ -66,6 +67,13 @@ struct ServerRT {
     std::thread worker;
     cudaStream_t stream = nullptr;
     size_t max_pending = 1 << 20;
+    // sizing of candidate micro-batches (host only): one for the worker, one
+    // for submit's check that a view fits the budget on its own
+    BatchRT *planner = nullptr, *submit_planner = nullptr;
+    std::mutex submit_mu;
+    // accounting (under mu)
+    uint64_t held_now = 0, held_peak = 0;
+    int64_t n_done = 0, n_batches = 0, n_busy = 0;
 
     // Two micro-batches alternate: while one runs on the device, the worker
     // gathers and enqueues the next (same stream, so the device runs them back
@@ -90,8 +98,27 @@ struct ServerRT {
         cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) return cuda_fail(e, "server stream");
         for (auto &sl : slots) sl.batch = new BatchRT(ctx, p);
+        planner = new BatchRT(ctx, p);
+        submit_planner = new BatchRT(ctx, p);
         worker = std::thread([this] { run(); });
         return ET_OK;
+    }
+
+    // Device bytes a batch of one view of n grains holds.
+    uint64_t single_view_bytes(int64_t n) {
+        std::lock_guard<std::mutex> g(submit_mu);
+        size_t sz[BatchRT::NGROUP];
+        submit_planner->plan_shape(1, n, n, (double)n * (double)n, sz);
+        uint64_t t = 0;
+        for (size_t v : sz) t += v;
+        return t;
+    }
+
+    void account() {
+        const uint64_t h = slots[0].batch->held_bytes() + slots[1].batch->held_bytes();
+        std::lock_guard<std::mutex> g(mu);
+        held_now = h;
+        held_peak = std::max(held_peak, h);
     }
 
     ~ServerRT() {
@@ -105,25 +132,56 @@ struct ServerRT {
             delete sl.batch;
             if (sl.xyz) cudaFreeHost(sl.xyz);
         }
+        delete planner;
+        delete submit_planner;
         if (stream) cudaStreamDestroy(stream);
     }
 
-    // Moves pending views into sl.take within the memory budget; waits for
-    // arrivals only if `wait` (nothing else is in flight).  False: stop.
-    bool gather(Slot &sl, bool wait) {
+    // Moves pending views into sl.take while the slot's planned device bytes
+    // plus the other slot's held bytes fit the budget; waits for arrivals
+    // only if `wait` (nothing else is in flight).  False: stop.
+    bool gather(Slot &sl, const Slot &other, bool wait) {
         sl.take.clear();
+        const uint64_t other_held = other.batch->held_bytes();
+        const uint64_t avail = budget > other_held ? budget - other_held : 0;
         std::unique_lock<std::mutex> g(mu);
         if (wait) cv_work.wait(g, [this] { return stop || !pending.empty(); });
         if (stop && pending.empty()) return false;
-        uint64_t bytes = 0;
+        long long n = 0, mx = 0;
+        double s2 = 0;
+        size_t sz[BatchRT::NGROUP];
         while (!pending.empty() && (int)sl.take.size() < max_views) {
-            uint64_t vb = view_bytes(p, pending.front().n);
-            if (!sl.take.empty() && bytes + vb > budget) break;
-            bytes += vb;
+            const long long vn = pending.front().n;
+            planner->plan_shape((int)sl.take.size() + 1, n + vn, std::max(mx, vn), s2 + (double)vn * vn, sz);
+            if (sl.batch->footprint_with(sz) > avail) break;
+            n += vn;
+            mx = std::max(mx, vn);
+            s2 += (double)vn * vn;
             sl.take.push_back(std::move(pending.front()));
             pending.pop_front();
         }
         return true;
+    }
+
+    void reject_oldest() {
+        std::lock_guard<std::mutex> g(mu);
+        if (pending.empty()) return;
+        Done d;
+        memset(&d.r, 0, sizeof d.r);
+        d.r.tag = pending.front().tag;
+        d.r.status = ET_ERR_OOM;
+        d.r.n_grains = pending.front().n;
+        d.r.t_submit_ns = pending.front().t_submit;
+        d.r.t_admit_ns = d.r.t_done_ns = now_ns();
+        pending.pop_front();
+        done.push_back(std::move(d));
+        ++n_done;
+        cv_done.notify_all();
+    }
+
+    bool has_pending() {
+        std::lock_guard<std::mutex> g(mu);
+        return !pending.empty();
     }
 
     void launch(Slot &sl) {
@@ -151,16 +209,23 @@ struct ServerRT {
                 if (!v.xyz.empty()) memcpy(sl.xyz + o, v.xyz.data(), v.xyz.size() * sizeof(int32_t));
                 o += v.xyz.size();
             }
+            const uint64_t other_held = slots[&sl == &slots[0] ? 1 : 0].batch->held_bytes();
+            sl.batch->byte_limit = budget > other_held ? budget - other_held : 1;
             sl.status = sl.batch->load(sl.xyz, sl.off.data(), (int)sl.take.size(), false, stream);
         }
         if (sl.status == ET_OK) sl.status = sl.batch->find(stream, false);
         sl.busy = true;
+        account();
     }
 
     void complete(Slot &sl, std::vector<int64_t> &vtrk, std::vector<et_track> &trk, std::vector<int32_t> &mem) {
         et_status s = sl.status;
         int64_t nt = 0, nm = 0;
         vtrk.assign(sl.take.size() + 1, 0);
+        {   // a re-run after an overflow may grow the slot only within what the other leaves
+            const uint64_t other_held = slots[&sl == &slots[0] ? 1 : 0].batch->held_bytes();
+            sl.batch->byte_limit = budget > other_held ? budget - other_held : 1;
+        }
         if (s == ET_OK) {
             s = sl.batch->fetch(vtrk.data(), nullptr, 0, &nt, nullptr, 0, &nm);
             if (s == ET_ERR_CAPACITY || s == ET_OK) {
@@ -197,10 +262,13 @@ struct ServerRT {
         {
             std::lock_guard<std::mutex> g(mu);
             for (auto &d : out) done.push_back(std::move(d));
+            n_done += (int64_t)out.size();
+            ++n_batches;
         }
         cv_done.notify_all();
         sl.take.clear();
         sl.busy = false;
+        account();
     }
 
     void run() {
@@ -212,7 +280,17 @@ struct ServerRT {
         for (;;) {
             Slot &sl = slots[cur], &other = slots[cur ^ 1];
             // wait for arrivals only when nothing is in flight
-            const bool live = gather(sl, !other.busy);
+            const bool live = gather(sl, other, !other.busy);
+            if (sl.take.empty() && has_pending()) {
+                // the oldest view does not fit beside the other slot: end the
+                // other slot's run, then free idle buffers, and try again
+                if (other.busy) complete(other, vtrk, trk, mem);
+                else if (other.batch->held_bytes() > 0) other.batch->release_groups();
+                else if (sl.batch->held_bytes() > 0) sl.batch->release_groups();
+                else reject_oldest();   // does not fit even alone (submit checks the same plan)
+                account();
+                continue;
+            }
             if (!sl.take.empty()) launch(sl);
             if (other.busy) complete(other, vtrk, trk, mem);
             if (!live && !sl.busy && !other.busy) return;
@@ -256,7 +334,11 @@ et_status et_server_create(et_ctx *ctx, const et_params *params, uint64_t mem_bu
 et_status et_server_submit(et_server *s, const int32_t *xyz, int64_t n, uint64_t tag) {
     if (!s || (n > 0 && !xyz) || n < 0) return fail(ET_ERR_INVALID_ARG, "bad submit arguments");
     if (n > (1 << 21) - 1) return fail(ET_ERR_INVALID_ARG, "view of %lld grains too large", (long long)n);
-    if (view_bytes(s->p, n) > s->budget) return fail(ET_ERR_BUSY, "view exceeds the memory budget on its own");
+    if (s->single_view_bytes(n) > s->budget) {
+        std::lock_guard<std::mutex> g(s->mu);
+        ++s->n_busy;
+        return fail(ET_ERR_BUSY, "view exceeds the memory budget on its own");
+    }
     Pending pv;
     pv.tag = tag;
     pv.n = n;
@@ -268,7 +350,10 @@ et_status et_server_submit(et_server *s, const int32_t *xyz, int64_t n, uint64_t
     }
     {
         std::lock_guard<std::mutex> g(s->mu);
-        if (s->pending.size() >= s->max_pending) return fail(ET_ERR_BUSY, "pending queue full");
+        if (s->pending.size() >= s->max_pending) {
+            ++s->n_busy;
+            return fail(ET_ERR_BUSY, "pending queue full");
+        }
         s->pending.push_back(std::move(pv));
     }
     s->cv_work.notify_one();
@@ -308,6 +393,27 @@ et_status et_server_fetch(et_server *s, uint64_t tag, et_track *tracks, int64_t 
         return fail(ET_ERR_CAPACITY, "need %lld tracks / %lld members", (long long)nt, (long long)nm);
     if (nt) memcpy(tracks, d.tracks.data(), sizeof(et_track) * nt);
     if (nm) memcpy(members, d.members.data(), sizeof(int32_t) * nm);
+    return ET_OK;
+}
+
+et_status et_server_set_max_pending(et_server *s, int64_t max_pending) {
+    if (!s || max_pending < 1) return fail(ET_ERR_INVALID_ARG, "server is NULL or max_pending < 1");
+    std::lock_guard<std::mutex> g(s->mu);
+    s->max_pending = (size_t)max_pending;
+    return ET_OK;
+}
+
+et_status et_server_get_stats(et_server *s, et_server_stats *out) {
+    if (!s || !out) return fail(ET_ERR_INVALID_ARG, "server/out is NULL");
+    std::lock_guard<std::mutex> g(s->mu);
+    memset(out, 0, sizeof *out);
+    out->budget_bytes = s->budget;
+    out->device_bytes = s->held_now;
+    out->peak_device_bytes = s->held_peak;
+    out->views_done = s->n_done;
+    out->batches = s->n_batches;
+    out->busy_rejections = s->n_busy;
+    out->pending = (int64_t)s->pending.size();
     return ET_OK;
 }
 

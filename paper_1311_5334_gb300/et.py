@@ -49,8 +49,8 @@ class Params(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("cell", C.c_int32 * 3), ("block_seeds", C.c_int32), ("row_lists", C.c_int32),
-                ("assoc_window", C.c_int32), ("reserved", C.c_int32 * 2)]
+    _fields_ = [("cell", C.c_int32 * 3), ("ticket_origins", C.c_int32), ("row_lists", C.c_int32),
+                ("assoc_window", C.c_int32), ("wait_polls", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,6 +67,12 @@ class Stats(C.Structure):
         d["cell"] = tuple(self.cell)
         d["stage_ms"] = dict(zip(self.STAGES, (float(x) for x in self.stage_ms))) if self.profiled else None
         return d
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("budget_bytes", C.c_uint64), ("device_bytes", C.c_uint64), ("peak_device_bytes", C.c_uint64),
+                ("views_done", C.c_int64), ("batches", C.c_int64), ("busy_rejections", C.c_int64),
+                ("pending", C.c_int64)]
 
 
 class Result(C.Structure):
@@ -140,6 +146,8 @@ _SIGS = {
     "et_server_fetch": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64, C.POINTER(C.c_int64),
                                     C.c_void_p, C.c_int64, C.POINTER(C.c_int64)]),
     "et_server_destroy": (C.c_int32, [C.c_void_p]),
+    "et_server_set_max_pending": (C.c_int32, [C.c_void_p, C.c_int64]),
+    "et_server_get_stats": (C.c_int32, [C.c_void_p, C.c_void_p]),
     "et_tube_count_noalloc": (C.c_int32, [C.c_void_p, C.c_int64, C.POINTER(Params), C.c_void_p, C.c_int64,
                                           C.c_void_p, C.c_void_p]),
     "et_probe_int_throughput": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double * 3)]),
@@ -314,12 +322,14 @@ class Batch:
         self._keep = None
         self.n_views = 0
 
-    def set_tuning(self, cell=(0, 0, 0), row_lists=0, assoc_window=0):
+    def set_tuning(self, cell=(0, 0, 0), row_lists=0, assoc_window=0, wait_polls=0, ticket_origins=0):
         t = Tuning()
+        t.ticket_origins = int(ticket_origins)
         for k in range(3):
             t.cell[k] = int(cell[k])
         t.row_lists = int(row_lists)
         t.assoc_window = int(assoc_window)
+        t.wait_polls = int(wait_polls)
         _check(lib().et_batch_set_tuning(self._h, C.byref(t)))
 
     def load(self, xyz, offsets, stream=None):
@@ -345,7 +355,7 @@ class Batch:
         t = Tuning()
         ms = C.c_float()
         _check(lib().et_batch_autotune(self._h, _stream_ptr(stream), int(max_trials), C.byref(t), C.byref(ms)))
-        self.tuning = {"cell": tuple(t.cell), "row_lists": int(t.row_lists)}
+        self.tuning = {"cell": tuple(t.cell), "row_lists": int(t.row_lists), "ticket_origins": int(t.ticket_origins)}
         return tuple(t.cell), float(ms.value)
 
     def sync(self):
@@ -457,6 +467,14 @@ class Server:
         _check(L.et_server_fetch(self._h, int(tag), _ptr(tracks), nt.value, C.byref(nt), _ptr(members),
                                  nm.value, C.byref(nm)))
         return tracks, members
+
+    def set_max_pending(self, n):
+        _check(lib().et_server_set_max_pending(self._h, int(n)))
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().et_server_get_stats(self._h, C.byref(st)))
+        return {k: int(getattr(st, k)) for k, _ in st._fields_}
 
     def close(self):
         if getattr(self, "_h", None):

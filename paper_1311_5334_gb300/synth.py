@@ -199,11 +199,19 @@ def batched(n_views=256, seed=3, sizes=None):
     rng = np.random.default_rng(seed)
     if sizes is None:
         sizes = lognormal_sizes(rng, n_views)
-    views = []
-    for i, nf in enumerate(sizes):
-        sub = np.random.default_rng([seed, i])
-        views.append(make_view(None, n_fog=int(nf), n_through=int(round(0.01 * nf)), rng=sub))
-    return views
+    return [batched_view(seed, i, int(nf)) for i, nf in enumerate(sizes)]
+
+
+def batched_view(seed, i, n_fog):
+    """View i of batched(seed=seed), whose fog count is n_fog (drawn by the
+    batch): views can be drawn independently, e.g. in parallel."""
+    sub = np.random.default_rng([seed, i])
+    return make_view(None, n_fog=int(n_fog), n_through=int(round(0.01 * n_fog)), rng=sub)
+
+
+def batched_sizes(n_views, seed):
+    """The fog counts batched(n_views, seed) draws."""
+    return lognormal_sizes(np.random.default_rng(seed), n_views)
 
 
 def stress(seed=5, n_fog=1_000_000, n_tracks=5000, short_frac=0.2) -> View:

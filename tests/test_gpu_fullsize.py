@@ -4,7 +4,8 @@ the launch configuration bench.py times: autotuned cells, CUDA-graph replay.
 Every view's complete result is compared with the oracle's: the per-seed
 table (seed_i, seed_j, count) of all 2.8e8 seeds as a multiset digest per
 view, and the full track list (seed pair, nhits, members, in acceptance
-order) as a SHA-256 per view.  The expected digests were written by
+order) as a SHA-256 per view, and the FP32 fit of three views with the
+oracle's FP64 fit.  The expected digests were written by
 tests/golden/make_fullsize_digests.py, which calls only the oracle (Section 2,
 Fig. 4 of the paper).  If the input generator draws a view differently on this
 platform (its input digest differs), that view's expected values are computed
@@ -100,3 +101,15 @@ def test_full_batched_workload_all_views(oracle_mod):
     assert st["n_seeds"] == tot_seeds == len(si)
     assert st["n_candidates"] == tot_cand
     assert st["n_tracks"] == tot_tracks
+    # the FP32 fit against the oracle's FP64 fit on the largest view and two others
+    from tests.test_gpu_parity import check_fit
+    sizes = np.array([v.n for v in views])
+    rng = np.random.default_rng(7)
+    for k in sorted({int(np.argmax(sizes))} | set(rng.choice(256, 2, replace=False).tolist())):
+        v = views[k]
+        o = oracle_mod.Oracle(v.xyz, p["extent"], p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"])
+        try:
+            want = o.find_tracks()
+        finally:
+            o.close()
+        check_fit(tracks[voff[k]:voff[k + 1]], want)
