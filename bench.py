@@ -273,7 +273,8 @@ def run_ours(args):
     batch.set_profiling(True)
     tuned = None
     if args.cell:
-        batch.set_tuning(tuple(int(c) for c in args.cell.split(",")), row_lists=args.rows)
+        batch.set_tuning(tuple(int(c) for c in args.cell.split(",")), row_lists=args.rows,
+                         ticket_origins=args.ticket_origins)
     batch.load(xyz_d, offs, stream=stream)
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
@@ -334,7 +335,8 @@ def run_ours(args):
         plain_views_per_s = e2e_val = None
         h2d = d2h = 0
     else:
-        tuning = (tuple(ref_stats["cell"]), batch.tuning["row_lists"] if tuned else args.rows)
+        tuning = (tuple(ref_stats["cell"]), batch.tuning["row_lists"] if tuned else args.rows,
+                  batch.tuning["ticket_origins"] if tuned else args.ticket_origins)
         plain_views_per_s, e2e_val, h2d, d2h = extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws,
                                                       tuning)
     line = {"metric": METRIC, "value": value, "unit": "views/s", "n_gpus": ws, "steps": args.steps,
@@ -494,7 +496,7 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
     n_views = len(views)
     # plain form: one view per launch sequence, same views, device-resident
     plain = et.Batch(ctx, params)
-    plain.set_tuning(tuning[0], row_lists=tuning[1])
+    plain.set_tuning(tuning[0], row_lists=tuning[1], ticket_origins=tuning[2])
     plain_ms = 0.0
     n_plain = min(n_views, int(os.environ.get("ET_PLAIN_VIEWS", "256")))
     for k in range(n_plain):
@@ -521,7 +523,7 @@ def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
     pinned = torch.from_numpy(xyz_h).pin_memory()
     host_view = pinned.numpy()
     eb = et.Batch(ctx, params)
-    eb.set_tuning(tuning[0], row_lists=tuning[1])
+    eb.set_tuning(tuning[0], row_lists=tuning[1], ticket_origins=tuning[2])
     eb.load(host_view, offs)
     eb.find(use_graph=True)
     tr, mem, voff = eb.fetch()
@@ -777,6 +779,8 @@ def main():
                     help="batched workload: time only its first N views (smaller profiling captures)")
     ap.add_argument("--cell", default="", help="cell edges x,y,z in coordinate units (default: automatic)")
     ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
+    ap.add_argument("--ticket-origins", type=int, default=0,
+                    help="with --cell: seed origins per work ticket (1, 2 or 4; 0 = automatic)")
     ap.add_argument("--served-views", type=int, default=10000,
                     help="distinct views of the served sweep (one run per rate of 100..5000 views/s)")
     ap.add_argument("--flags", type=int, default=0,

@@ -395,8 +395,8 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
 //
 // Seeds (Section 2) are the pairs of grains of one view with
 // seed_min^2 <= |g_b - g_a|^2 < seed_max^2, each pair once (a of lower
-// canonical rank).  A warp takes b.gen_origins origins a at a time (1, 2 or 4,
-// a tuning choice; consecutive in the
+// canonical rank).  A warp takes SG origins a at a time (1, 2 or 4, a tuning
+// choice compiled into one kernel each; consecutive in the
 // x-row cell order, one work ticket).  The cell rows that can hold their
 // partners -- the (y, z) cells within seed_max - 1 of a, each an x run from
 // a's cell to the largest admissible dx -- are dealt to the lanes in rounds
@@ -405,9 +405,9 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
 // in shared memory; the tube walk takes them 32 at a time.  So seeds are
 // walked in the order origin, row, x, and concurrently running warps work on
 // nearby origins: no seed list is written to memory.
-constexpr int SG = 4;          // most origins per work ticket (b.gen_origins: 1, 2 or 4)
 constexpr int SQ = 64;         // seed queue: < 32 waiting + one pass
 
+template <int SG>
 struct GenSm {
     int4 og[SG];      // origin: x, y, z, canonical index
     int4 oc[SG];      // cx0, cx1, cy0, cz0
@@ -429,17 +429,18 @@ struct GenState {
     u32 pair_tests = 0;   // seed-window tests made by this lane (far below 2^32 in one launch)
 };
 
-// Takes the next b.gen_origins origins; false when none is left.
-__device__ __forceinline__ bool gen_group(const Batch &b, GenSm &sm, GenState &gs) {
+// Takes the next SG origins; false when none is left.
+template <int SG>
+__device__ __forceinline__ bool gen_group(const Batch &b, GenSm<SG> &sm, GenState &gs) {
     const int lane = threadIdx.x & 31;
     u64 g0 = 0;
-    if (lane == 0) g0 = atomicAdd(&b.ctl->ticket[0], (u64)b.gen_origins);
+    if (lane == 0) g0 = atomicAdd(&b.ctl->ticket[0], (u64)SG);
     g0 = __shfl_sync(0xffffffffu, g0, 0);
     const u64 N = (u64)b.N;
     if (g0 >= N) return false;
     const int reach = b.smax - 1;   // >= 0: seed_max >= 1
     int nrows = 0;
-    if (lane < b.gen_origins && g0 + lane < N) {
+    if (lane < SG && g0 + lane < N) {
         const int4 g = b.gc[g0 + lane];
         const int v = view_of(b.goff, b.V, g.w);
         const int cx0 = g.x / b.cs[0];
@@ -469,7 +470,8 @@ __device__ __forceinline__ bool gen_group(const Batch &b, GenSm &sm, GenState &g
 }
 
 // Resolves the rows of the round at gs.ibase into the pass table.
-__device__ __forceinline__ void gen_round(const Batch &b, GenSm &sm, GenState &gs) {
+template <int SG>
+__device__ __forceinline__ void gen_round(const Batch &b, GenSm<SG> &sm, GenState &gs) {
     const int lane = threadIdx.x & 31;
     const unsigned lane_lt = (1u << lane) - 1u;
     const int item = gs.ibase + lane;
@@ -514,7 +516,8 @@ __device__ __forceinline__ void gen_round(const Batch &b, GenSm &sm, GenState &g
 
 // One pass of 32 grain tests, appending the accepted pairs to the queue;
 // false when every origin is done.
-__device__ __forceinline__ bool gen_pass(const Batch &b, GenSm &sm, GenState &gs) {
+template <int SG>
+__device__ __forceinline__ bool gen_pass(const Batch &b, GenSm<SG> &sm, GenState &gs) {
     while (gs.pbase >= gs.rtotal) {
         gs.ibase += 32;
         if (gs.ibase >= gs.gtotal && !gen_group(b, sm, gs)) return false;
@@ -554,12 +557,13 @@ __device__ __forceinline__ bool gen_pass(const Batch &b, GenSm &sm, GenState &gs
     return true;
 }
 
+template <int SG>
 __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int record) {
     if (input_failed(b.ctl)) return;
     __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
     __shared__ u32 scount[TW][32];
-    __shared__ GenSm gsm[TW];
+    __shared__ GenSm<SG> gsm[TW];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     u32 tests = 0, hits = 0;   // per thread: far below 2^32 in one launch
     u64 nseeds = 0;            // per warp (lane 0)
@@ -717,7 +721,9 @@ unsigned persistent_grid(int blocks_per_sm) {
 }  // namespace
 
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st) {
-    k_tube_count<<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
+    if (b.gen_origins == 1) k_tube_count<1><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
+    else if (b.gen_origins == 4) k_tube_count<4><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
+    else k_tube_count<2><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
 }
 
 void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st) {
