@@ -47,12 +47,13 @@ OPS_PER_TEST = 14
 OPS_PER_PAIR_TEST = 6
 # DRAM bytes one launch of the tube-count kernel (seed generation and tube
 # counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
-# capture of that launch (one pass, the first timed step):
-#   batched  611.68 MB + 45.84 MB  (256 views, autotuned cells 74x621x506, both lists)
+# capture of that launch (one pass, the first timed step, the kernel as built
+# now; profiles/k_tube_count_batched.md):
+#   batched  613.37 MB + 45.85 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
 # The kernel reads each view's grains and cell tables about once, so the bytes
 # follow the views and the cell shape rather than the seeds; workloads without
 # a capture of their own launch report null.
-TUBE_DRAM_BYTES = {"batched": 611.68e6 + 45.84e6}
+TUBE_DRAM_BYTES = {"batched": 613.37e6 + 45.85e6}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
