@@ -58,7 +58,7 @@ typedef int32_t et_status;
 #define ET_ERR_INVALID_ARG      -1  /* null pointer, bad size or parameter */
 #define ET_ERR_OUT_OF_RANGE     -2  /* a coordinate outside [0, extent) */
 #define ET_ERR_DUPLICATE_GRAIN  -3  /* two grains with identical coordinates in one view */
-#define ET_ERR_PRECONDITION     -4  /* parameters break the int32 cross-product bound */
+#define ET_ERR_PRECONDITION     -4  /* parameters break an integer bound of the exact test */
 #define ET_ERR_CAPACITY         -5  /* a caller buffer is too small; required sizes returned */
 #define ET_ERR_OOM              -6  /* device memory could not be allocated */
 #define ET_ERR_BUSY             -7  /* server memory budget or queue full; retry later */
@@ -90,8 +90,9 @@ typedef int32_t et_status;
  *   extent[k] <= 2^21, views of at most 2^21 - 1 grains,
  *   0 <= seed_min <= seed_max, 1 <= seed_max, 0 <= tube_r <= 2^20, 1 <= min_hits,
  *   (extent[a] + extent[b]) * seed_max < 2^31 for every pair of axes a != b
- *   (so every cross-product component is an exact int32), else
- *   ET_ERR_PRECONDITION.  flags: a combination of the ET_FLAG_* bits above.
+ *   (so every cross-product component is an exact int32) and
+ *   3 tube_r^2 seed_max^2 < 2^63 (so the tube bound r^2 |w|^2 is an exact
+ *   int64), else ET_ERR_PRECONDITION.  flags: a combination of the ET_FLAG_* bits above.
  *   With ET_FLAG_ANGLE_CUT: 0 <= cut_base <= 2^21, 0 <= cut_slope <= 2^20,
  *   0 <= cut_tan_max <= 1024 (cut fields are ignored without it); reserved = 0. */
 typedef struct {

@@ -100,6 +100,11 @@ et_status check_params(const et_params *p) {
                         p->cut_slope, p->cut_tan_max);
     }
     if (p->reserved != 0) return fail(ET_ERR_INVALID_ARG, "reserved field must be 0");
+    {   // r^2 |w|^2 of a seed (|w_e| < seed_max) must stay below 2^63
+        const double rr = (double)p->tube_r * (double)p->tube_r * 3.0 * (double)p->seed_max * (double)p->seed_max;
+        if (rr >= 9.2e18)
+            return fail(ET_ERR_PRECONDITION, "3 tube_r^2 seed_max^2 = %.3g >= 2^63: the tube bound leaves int64", rr);
+    }
     for (int a = 0; a < 3; ++a)
         for (int c = a + 1; c < 3; ++c) {
             long long v = ((long long)p->extent[a] + p->extent[c]) * (long long)p->seed_max;
@@ -242,6 +247,7 @@ et_status BatchRT::autotune(cudaStream_t st, int max_trials, et_tuning *chosen, 
         }
     }
     profile = saved_prof;
+    if (best_t.ticket_origins == 0) best_t.ticket_origins = 2;   // the automatic choice, made explicit
     tune = best_t;
     choose_cells();
     et_status s = reserve();

@@ -4,7 +4,9 @@
 // through g_a with direction w = g_b - g_a iff
 //     |(g_k - g_a) x w|^2 <= r^2 |w|^2 .
 // Cross-product components are exact int32 under the parameter precondition
-// (|d_e w_f| + |d_f w_e| < 2^31); squares and their sum are int64.
+// (|d_e w_f| + |d_f w_e| < 2^31); each square is below 2^62, so their sum is
+// below 3 * 2^62 and exact in unsigned 64 bits, and so is r^2 |w|^2 (the
+// parameters keep 3 r^2 seed_max^2 below 2^63).
 //
 // Cover.  The tube is an infinite cylinder across the view.  A grain p in the
 // tube has a foot point q(t) = g_a + t w with |p - q| <= r, so on every axis
@@ -29,8 +31,10 @@ __device__ __forceinline__ bool in_tube(int4 g, int3 a, int3 w, long long R) {
     const int cx = dy * w.z - dz * w.y;
     const int cy = dz * w.x - dx * w.z;
     const int cz = dx * w.y - dy * w.x;
-    const long long s = (long long)cx * cx + (long long)cy * cy + (long long)cz * cz;
-    return s <= R;
+    const unsigned long long s = (unsigned long long)((long long)cx * cx) +
+                                 (unsigned long long)((long long)cy * cy) +
+                                 (unsigned long long)((long long)cz * cz);
+    return s <= (unsigned long long)R;
 }
 
 __device__ __forceinline__ int floor_i(float x) { return __float2int_rd(x); }
