@@ -285,6 +285,31 @@ def test_empty_and_tiny_views(et, ctx):
     assert et.track_tuples(tracks, members) == [(1, 0, 2, (0, 1))]
 
 
+def test_batch_with_empty_and_single_grain_views(et, ctx, oracle_mod):
+    """Ragged batches: empty views and one-grain views between real ones, first
+    and last, plain and replayed from a graph; offsets must stay consistent."""
+    real = [v for v in synth.batched(n_views=12, seed=12) if v.n < 20000][:3]
+    assert len(real) == 3
+    one = np.array([[123, 456, 789]], dtype=np.int32)
+    none = np.zeros((0, 3), dtype=np.int32)
+    xyzs = [none, real[0].xyz, one, none, none, real[1].xyz, one, real[2].xyz, none]
+    offs = np.concatenate([[0], np.cumsum([len(x) for x in xyzs])]).astype(np.int64)
+    xyz = np.concatenate(xyzs).astype(np.int32)
+    p = synth.params(real[0].extent)
+    want = [oracle_run(oracle_mod, x, p).as_tuples() if len(x) > 1 else [] for x in xyzs]
+    b = et.Batch(ctx, p)
+    try:
+        b.load(xyz, offs)
+        for use_graph in (False, True, True):
+            b.find(use_graph=use_graph)
+            tracks, members, voff = b.fetch()
+            assert len(voff) == len(xyzs) + 1 and voff[0] == 0 and voff[-1] == len(tracks)
+            for k in range(len(xyzs)):
+                assert et.track_tuples(tracks[voff[k]:voff[k + 1]], members) == want[k], k
+    finally:
+        b.close()
+
+
 def test_long_collinear_line(et, ctx, oracle_mod):
     """4000 collinear grains: every seed holds all of them; one track."""
     n = 4000
