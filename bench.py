@@ -249,7 +249,7 @@ def run_ours(args):
     ws, rank, local = dist_env()
     # the served sweep's views are drawn by spawned processes before any CUDA call
     served_pool = None
-    if not args.no_extra and args.workload == "batched":
+    if not args.no_extra and args.workload == "batched" and ws == 1:   # a one-GPU measurement
         served_pool = served_views_pool(args.served_views, seed=4)
     torch.cuda.set_device(local)
     dist = None
@@ -385,7 +385,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(ref_stats["kernel_launches"]) * args.steps,
             "clocks": clk}
-    if not args.no_extra and args.workload == "batched":
+    if served_pool is not None:
         line["served"] = served_sweep(ctx, params, served_pool)
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra and args.workload == "stress":
