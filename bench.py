@@ -49,11 +49,11 @@ OPS_PER_PAIR_TEST = 6
 # counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of that launch (one pass, the first timed step, the kernel as built
 # now; profiles/k_tube_count_batched.md):
-#   batched  613.37 MB + 45.85 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
+#   batched  613.30 MB + 45.13 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
 # The kernel reads each view's grains and cell tables about once, so the bytes
 # follow the views and the cell shape rather than the seeds; workloads without
 # a capture of their own launch report null.
-TUBE_DRAM_BYTES = {"batched": 613.37e6 + 45.85e6}
+TUBE_DRAM_BYTES = {"batched": 613.30e6 + 45.13e6}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
@@ -387,6 +387,7 @@ def run_ours(args):
             "clocks": clk}
     if served_pool is not None:
         line["served"] = served_sweep(ctx, params, served_pool)
+        line["other_workloads"] = other_workloads(ctx, stream)
     line.update(line_extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not args.no_extra and args.workload == "stress":
         # one stress view is the oracle's smallest unit of work and takes it far
@@ -498,6 +499,66 @@ def pinned_array(n, dtype):
 
 
 pinned_array.keep = []
+
+
+def other_workloads(ctx, stream, local=0):
+    """The one-view workloads (PR1, dense, stress) in the same run: graph
+    replay of the whole path on device-resident grains with the autotuner's
+    choice for each view, CUDA events over K steps (enough for the clock
+    sampler).  views/s, ms per step, stage times, ALU roofline fraction and
+    the clocks seen."""
+    import torch
+    from paper_1311_5334_gb300 import et
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for name, steps in (("pr1", 3000), ("dense", 800), ("stress", 5)):
+        v = {"pr1": synth.pr1, "dense": synth.dense, "stress": synth.stress}[name]()
+        p = synth.params(v.extent)
+        xyz_d = torch.from_numpy(v.xyz).cuda()
+        b = et.Batch(ctx, p)
+        try:
+            b.set_profiling(True)
+            b.load(xyz_d, [0, v.n], stream=stream)
+            cell, _ = b.autotune(stream=stream)
+            for _ in range(3):
+                b.load(xyz_d, [0, v.n], stream=stream)
+                b.find(stream=stream, use_graph=True)
+                b.sync()
+            st = b.stats()
+            clocks = ClockSampler(local)
+            clocks.start()
+            torch.cuda.synchronize()
+            ms = 0.0
+            for _ in range(steps):
+                if name == "stress":
+                    flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.load(xyz_d, [0, v.n], stream=stream)
+                b.find(stream=stream, use_graph=True)
+                e1.record(stream)
+                if name == "stress":
+                    b.sync()
+                    ms += e0.elapsed_time(e1)
+                else:
+                    e1.synchronize()
+                    ms += e0.elapsed_time(e1)
+            b.sync()
+            clk = clocks.stop()
+            st2 = b.stats()
+        finally:
+            b.close()
+        tube_ms = st2["stage_ms"]["tube_count"]
+        ops = OPS_PER_TEST * st["n_tests"] + OPS_PER_PAIR_TEST * st["n_pair_tests"]
+        peak = 152 * 128 * 2070e6
+        out[name] = {"views_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps, "grains": v.n,
+                     "tuning": {"cell": list(cell), "row_lists": b.tuning["row_lists"],
+                                "ticket_origins": b.tuning["ticket_origins"]},
+                     "seeds": st["n_seeds"], "tracks": st["n_tracks"], "stage_ms": st2["stage_ms"],
+                     "alu_frac": ops / (tube_ms / 1e3) / peak, "clocks": clk,
+                     "l2": "flushed between steps" if name == "stress" else "view resident in L2 between steps"}
+    return out
 
 
 def extras(args, ctx, params, views, xyz_h, xyz_d, offs, stream, ws, tuning):
