@@ -1,14 +1,15 @@
 """Writes the expected full-size results of the batched workload (256 views of
-300x300x50 um, seed 3) and the stress workload (one 1000x1000x50 um view,
-seed 5) as digests: fullsize_batched_seed3.json and fullsize_stress_seed5.json
-beside this script.
+300x300x50 um, seed 3), of the first 256 views of the served workload (the
+batched size law, seed 4) and of the stress workload (one 1000x1000x50 um
+view, seed 5) as digests: fullsize_batched_seed3.json,
+fullsize_served_seed4.json and fullsize_stress_seed5.json beside this script.
 
 Every expected value comes from the CPU oracle (oracle/), which evaluates the
 definition of Section 2 and Fig. 4 of the paper: seeds in the distance window,
 exact tube counts over all grains, threshold, sequential greedy exclusive
 association.  Nothing here calls the CUDA library.
 
-  python tests/golden/make_fullsize_digests.py [batched|stress|all] [--threads T]
+  python tests/golden/make_fullsize_digests.py [batched|served|stress|all] [--threads T]
 
 Takes minutes on a multi-core host (the per-seed tube counts run on all cores).
 """
@@ -52,7 +53,7 @@ def view_record(v, p, threads):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", nargs="?", default="all", choices=["batched", "stress", "all"])
+    ap.add_argument("which", nargs="?", default="all", choices=["batched", "served", "stress", "all"])
     ap.add_argument("--threads", type=int, default=0)
     a = ap.parse_args()
     O.build()
@@ -69,6 +70,21 @@ def main():
                "source": "oracle/oracle.c via oracle.Oracle.find_tracks(keep_seeds=True)",
                "views": recs}
         with open(os.path.join(HERE, "fullsize_batched_seed3.json"), "w") as f:
+            json.dump(out, f, indent=0)
+    if a.which in ("served", "all"):
+        t0 = time.time()
+        views = synth.batched(n_views=256, seed=4)
+        p = synth.params(views[0].extent)
+        recs = []
+        for k, v in enumerate(views):
+            recs.append(view_record(v, p, a.threads))
+            print(f"served view {k}: {v.n} grains, {recs[-1]['n_tracks']} tracks "
+                  f"({time.time() - t0:.0f} s)", flush=True)
+        out = {"workload": "served: synth.batched(n_views=256, seed=4) (the first 256 views of the served "
+                           "stream), synth.params",
+               "source": "oracle/oracle.c via oracle.Oracle.find_tracks(keep_seeds=True)",
+               "views": recs}
+        with open(os.path.join(HERE, "fullsize_served_seed4.json"), "w") as f:
             json.dump(out, f, indent=0)
     if a.which in ("stress", "all"):
         t0 = time.time()
