@@ -407,6 +407,7 @@ def run_ours(args):
         d1, s1, t1, names1 = oracle_views_per_s(views, budget / 2, args=args, threads=1)
         line["cpu_baseline_1thread"] = {"value": d1 / t1, "unit": "views/s", "cores": 1, "kind": "oracle",
                                         "seeds_per_s": s1 / t1,
+                                        "views_per_s_at_the_step_mean": (s1 / t1) / (ref_stats["n_seeds"] / n_views),
                                         "sample": f"views {names1[0]}..{names1[-1]} ({d1} of {n_views}) "
                                                   f"of the step, {t1:.1f} s, one thread"}
     batch.close()

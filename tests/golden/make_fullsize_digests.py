@@ -9,7 +9,11 @@ definition of Section 2 and Fig. 4 of the paper: seeds in the distance window,
 exact tube counts over all grains, threshold, sequential greedy exclusive
 association.  Nothing here calls the CUDA library.
 
-  python tests/golden/make_fullsize_digests.py [batched|served|stress|all] [--threads T]
+  python tests/golden/make_fullsize_digests.py [batched|served|stress|variants|all] [--threads T]
+
+"variants" writes fullsize_variants_seed3.json: the track-list digests of the
+batched workload under the single-pass association (flags 1) and under the
+sequential association with the grain-count cut (flags 2, cut 9, 3, 4).
 
 Takes minutes on a multi-core host (the per-seed tube counts run on all cores).
 """
@@ -53,7 +57,7 @@ def view_record(v, p, threads):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", nargs="?", default="all", choices=["batched", "served", "stress", "all"])
+    ap.add_argument("which", nargs="?", default="all", choices=["batched", "served", "stress", "variants", "all"])
     ap.add_argument("--threads", type=int, default=0)
     a = ap.parse_args()
     O.build()
@@ -85,6 +89,27 @@ def main():
                "source": "oracle/oracle.c via oracle.Oracle.find_tracks(keep_seeds=True)",
                "views": recs}
         with open(os.path.join(HERE, "fullsize_served_seed4.json"), "w") as f:
+            json.dump(out, f, indent=0)
+    if a.which in ("variants", "all"):
+        t0 = time.time()
+        views = synth.batched(n_views=256, seed=3)
+        out = {"workload": "batched: synth.batched(n_views=256, seed=3) under association variants",
+               "source": "oracle/oracle.c via oracle.Oracle.find_tracks with flags and cut", "variants": {}}
+        for name, flags, cut in (("single_pass", 1, (0, 0, 0)), ("angle_cut_9_3_4", 2, (9, 3, 4))):
+            p = synth.params(views[0].extent, flags=flags, cut=cut)
+            recs = []
+            for k, v in enumerate(views):
+                o = O.Oracle(v.xyz, p["extent"], p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"],
+                             flags=flags, cut=cut)
+                try:
+                    tr = o.find_tracks(nthreads=a.threads)
+                finally:
+                    o.close()
+                recs.append({"input_sha256": fullsize.input_digest(v.xyz), "n_tracks": len(tr),
+                             "tracks_sha256": fullsize.track_digest(tr.as_tuples())})
+            print(f"{name}: {sum(r['n_tracks'] for r in recs)} tracks ({time.time() - t0:.0f} s)", flush=True)
+            out["variants"][name] = {"flags": flags, "cut": list(cut), "views": recs}
+        with open(os.path.join(HERE, "fullsize_variants_seed3.json"), "w") as f:
             json.dump(out, f, indent=0)
     if a.which in ("stress", "all"):
         t0 = time.time()

@@ -5,7 +5,8 @@ Every view's complete result is compared with the oracle's: the per-seed
 table (seed_i, seed_j, count) of all 2.8e8 seeds as a multiset digest per
 view, and the full track list (seed pair, nhits, members, in acceptance
 order) as a SHA-256 per view, and the FP32 fit of three views with the
-oracle's FP64 fit.  The expected digests were written by
+oracle's FP64 fit; under the two association variants (single pass, and the
+grain-count cut) the complete track lists of all views as well.  The expected digests were written by
 tests/golden/make_fullsize_digests.py, which calls only the oracle (Section 2,
 Fig. 4 of the paper).  If the input generator draws a view differently on this
 platform (its input digest differs), that view's expected values are computed
@@ -113,3 +114,41 @@ def test_full_batched_workload_all_views(oracle_mod):
         finally:
             o.close()
         check_fit(tracks[voff[k]:voff[k + 1]], want)
+
+
+@pytest.mark.parametrize("name", ["single_pass", "angle_cut_9_3_4"])
+def test_full_batched_workload_variants(oracle_mod, name):
+    """The association variants (single pass; sequential with the grain-count
+    cut) on all 256 views: every view's complete track list against the
+    oracle's digest in the same mode."""
+    from paper_1311_5334_gb300 import et
+    with open(os.path.join(GOLD, "fullsize_variants_seed3.json")) as f:
+        gold = json.load(f)["variants"][name]
+    views = synth.batched(n_views=256, seed=3)
+    xyz, offs = synth.concat(views)
+    p = synth.params(views[0].extent, flags=gold["flags"], cut=tuple(gold["cut"]))
+    with et.Context(0) as ctx:
+        b = et.Batch(ctx, p)
+        try:
+            b.load(xyz, offs)
+            b.autotune()
+            for _ in range(2):   # capture, then replay
+                b.load(xyz, offs)
+                b.find(use_graph=True)
+            tracks, members, voff = b.fetch()
+        finally:
+            b.close()
+    for k, v in enumerate(views):
+        g = gold["views"][k]
+        if g["input_sha256"] == fullsize.input_digest(v.xyz):
+            want, n_want = g["tracks_sha256"], g["n_tracks"]
+        else:
+            o = oracle_mod.Oracle(v.xyz, p["extent"], p["seed_min"], p["seed_max"], p["tube_r"], p["min_hits"],
+                                  flags=p["flags"], cut=p["cut"])
+            try:
+                t = o.find_tracks().as_tuples()
+            finally:
+                o.close()
+            want, n_want = fullsize.track_digest(t), len(t)
+        got = et.track_tuples(tracks[voff[k]:voff[k + 1]], members)
+        assert len(got) == n_want and fullsize.track_digest(got) == want, f"{name}: view {k} ({v.n} grains)"
