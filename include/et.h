@@ -124,7 +124,8 @@ typedef struct {
                                rounds run window by window in candidate order); 0: automatic
                                (at least 2^18, at most 128 windows) */
     int32_t wait_polls;     /* 0: default.  Otherwise every bounded device-side wait (the
-                               association's grid barrier, the sorts' look-back) gives up
+                               grid barriers of the association, the sorts and the scans;
+                               the sorts' look-back) gives up
                                after this many polls and the run fails with ET_ERR_TIMEOUT.
                                Small values make a wait run out on purpose (tests of the
                                timeout path); the next run with 0 is unaffected */

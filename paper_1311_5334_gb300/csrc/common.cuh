@@ -39,8 +39,7 @@ struct Ctl {
     u64 n_record;       // per-seed records written (diagnostic path)
     u32 error;          // ERRB_* bits
     u32 rounds;         // merge rounds run
-    u32 bar_count;      // grid barrier arrivals
-    u32 bar_gen;        // grid barrier generation
+    u32 bar[2];         // grid barrier of the cooperative kernels: arrivals, generation
     u32 active[2];      // merge: participants per round (ping-pong)
     u32 pad[2];
     u64 ncl[2];         // merge: lengths of the undecided-candidate lists (ping-pong)
@@ -155,29 +154,84 @@ __device__ __forceinline__ bool input_failed(const Ctl *ctl) {
     return (*(volatile const u32 *)&ctl->error & (ERRB_INPUT_MASK | ERRB_OVF_MASK | ERRB_TIMEOUT)) != 0;
 }
 
+// Bounded grid barrier over the first nblocks blocks of a cooperative launch.
+// bar[0] counts arrivals and is 0 between barriers (it must be 0 before a
+// launch's first barrier); bar[1] is a generation that only grows.  A block
+// that polls more than lim times, or sees err_bit set by another block, sets
+// err_bit and returns false: the caller must then return.  With one block the
+// barrier is a block barrier.
+__device__ __forceinline__ bool coop_barrier(u32 *bar, unsigned nblocks, u32 *err, u32 err_bit,
+                                             unsigned long long lim) {
+    __syncthreads();
+    if (nblocks > 1 && threadIdx.x == 0) {
+        volatile u32 *gen = &bar[1];
+        const u32 g = *gen;
+        __threadfence();
+        const u32 arrived = atomicAdd(&bar[0], 1u);
+        if (arrived == nblocks - 1) {
+            bar[0] = 0;
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == g) {
+                if (++spins > lim || (*(volatile u32 *)err & err_bit)) {
+                    atomicOr(err, err_bit);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return (*(volatile u32 *)err & err_bit) == 0;
+}
+
+// Blocks of a cooperative launch of kernel fn with the given block size that
+// fit on the device at once (0 if the query fails).
+template <class F>
+inline unsigned coop_grid_limit(F fn, int threads) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    return sms > 0 && per_sm > 0 ? (unsigned)(sms * per_sm) : 0u;
+}
+
 // ---------------------------------------------------------------- launchers
 // scan_sort.cu
+// Queries the cooperative launch limits of the scan and the sort (call once
+// per process before any capture).
+void init_scan_sort();
 size_t radix_temp_bytes(long long n);
-// Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key.
-// Ping-pongs between (k0, v0) and (k1, v1); returns 0 if the result is in
-// (k0, v0), 1 if in (k1, v1).  A pass whose tile polls a predecessor more
-// than spin_limit times (0: the default limit, about half a second) sets
-// err_bit in *err; the result is then invalid, but every write stays inside
+// Stable LSD radix sort of (key, value) pairs on bits [0, bits) of the key,
+// over [0, min(*n_dev, n_cap)) (all n_cap when n_dev is null), in one
+// cooperative launch.  Ping-pongs between (k0, v0) and (k1, v1); returns 0 if
+// the result is in (k0, v0), 1 if in (k1, v1).  bar: two words of zero (a
+// completed sort leaves them zero).  A wait (grid barrier, or a tile's wait
+// on a predecessor) that polls more than spin_limit times (0: the default
+// limit, about half a second) sets err_bit in *err and the sort stops; if
+// err_bit is already set the sort does nothing.  Every write stays inside
 // [0, n).
-int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp,
-                     cudaStream_t st, u32 *err, u32 err_bit, long long spin_limit = 0);
-size_t scan_temp_bytes(long long n);
-// Exclusive prefix sum of n values; writes n + 1 outputs (the last = total).
-// In place allowed.
-void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaStream_t st);
-// Same for u64 over [0, min(*n_dev, n_cap)) when n_dev is not null; the total
-// is also stored in *total_out when total_out is not null.
-void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
-                            u64 *total_out, cudaStream_t st);
 int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, const u64 *n_dev, int bits,
-                         void *temp, cudaStream_t st, u32 *err, u32 err_bit, long long spin_limit = 0);
-// Kernel launches of one radix sort on bits bits (histogram, bases, passes).
-inline int radix_sort_launches(int bits) { return bits > 0 ? 2 + (bits + 7) / 8 : 0; }
+                         void *temp, cudaStream_t st, u32 *err, u32 err_bit, u32 *bar, long long spin_limit = 0);
+inline int radix_sort_pairs(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n, int bits, void *temp,
+                            cudaStream_t st, u32 *err, u32 err_bit, u32 *bar, long long spin_limit = 0) {
+    return radix_sort_pairs_dev(k0, v0, k1, v1, n, nullptr, bits, temp, st, err, err_bit, bar, spin_limit);
+}
+// Kernel launches of one radix sort on bits bits.
+inline int radix_sort_launches(int bits) { return bits > 0 ? 1 : 0; }
+size_t scan_temp_bytes(long long n);
+// Exclusive prefix sum of the first min(*n_dev, n_cap) values (n_cap when
+// n_dev is null) in one cooperative launch; writes n + 1 outputs (the last =
+// total), and the total to *total_out when total_out is not null.  In place
+// allowed.  bar, err, err_bit and spin_limit as for the sort.
+void exclusive_scan_u32(const u32 *in, u32 *out, long long n, void *temp, cudaStream_t st, u32 *err,
+                        u32 err_bit, u32 *bar, long long spin_limit = 0);
+void exclusive_scan_u64_dev(const u64 *in, u64 *out, long long n_cap, const u64 *n_dev, void *temp,
+                            u64 *total_out, cudaStream_t st, u32 *err, u32 err_bit, u32 *bar,
+                            long long spin_limit = 0);
 
 // grid.cu
 void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st);

@@ -55,6 +55,7 @@ struct FrCtl {
     u64 n_grains;   // grains appended (may exceed the capacity)
     u64 n_cand;     // voxels with f > T
     u32 error;      // FRB_* bits
+    u32 bar[2];     // grid barrier of the sort and the scan
     u32 pad;
 };
 
@@ -548,11 +549,12 @@ struct FramesRT {
         cudaEventRecord(ev[2], st);
         const int bits = bits_for((u64)V * p.depth * p.height * p.width - 1);
         sorted = radix_sort_pairs_dev(keys[0], vals[0], keys[1], vals[1], (long long)cap, &ctl->n_grains, bits,
-                                      temp, st, &ctl->error, FRB_TIMEOUT);
-        // recognition, the sort, the gather and the 3-kernel scan of the view counts
-        launches = 1 + radix_sort_launches(bits) + 1 + 3;
+                                      temp, st, &ctl->error, FRB_TIMEOUT, ctl->bar);
+        // recognition, the sort, the gather and the scan of the view counts
+        launches = 1 + radix_sort_launches(bits) + 1 + 1;
         k_fr_gather<<<152 * 4, 256, 0, st>>>(ctl, cap, vals[sorted], rec, xyz, pulse);
-        exclusive_scan_u32(view_count, view_off, (long long)V, temp, st);   // view_off[V] = total
+        exclusive_scan_u32(view_count, view_off, (long long)V, temp, st, &ctl->error, FRB_TIMEOUT,
+                           ctl->bar);   // view_off[V] = total
         cudaError_t e = cudaGetLastError();
         return e == cudaSuccess ? ET_OK : cuda_fail(e, "front-end launch");
     }

@@ -29,7 +29,9 @@
 // until its decision.
 //
 // Rounds are separated by a grid barrier in one cooperative launch; every
-// wait is bounded and a timeout sets ERRB_TIMEOUT instead of hanging.
+// wait is bounded and a timeout sets ERRB_TIMEOUT instead of hanging.  The
+// launch covers the device; a short candidate list keeps only a few of its
+// blocks (the result does not depend on how many).
 #include "common.cuh"
 #include <math.h>
 
@@ -51,44 +53,23 @@ constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 24;  // x ~128 ns slee
 
 __device__ __forceinline__ u32 ld_cg_u32(const u32 *p) { return __ldcg(p); }
 
-// Grid-wide barrier for a cooperative launch.  Returns false if it timed out
-// (polls beyond the limit; 0: the default of about 2 s) or another block
-// recorded a timeout: the caller must then return.
-__device__ bool grid_barrier(Ctl *ctl, unsigned nblocks, long long limit) {
-    const unsigned long long lim = limit > 0 ? (unsigned long long)limit : BARRIER_SPIN_LIMIT;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile u32 *gen = &ctl->bar_gen;
-        const u32 g = *gen;
-        __threadfence();
-        const u32 arrived = atomicAdd(&ctl->bar_count, 1u);
-        if (arrived == nblocks - 1) {
-            ctl->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ctl->bar_gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*gen == g) {
-                if (++spins > lim || (*(volatile u32 *)&ctl->error & ERRB_TIMEOUT)) {
-                    atomicOr(&ctl->error, ERRB_TIMEOUT);
-                    break;
-                }
-                __nanosleep(128);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return (*(volatile u32 *)&ctl->error & ERRB_TIMEOUT) == 0;
-}
+// Candidates per block in use: the association keeps one block per MT / 32
+// candidates (one candidate per warp, whose dependent loads are the round's
+// latency), so a short candidate list runs on few blocks whose barriers are
+// cheap, a long one on the whole grid.
+constexpr u64 MERGE_CANDS_PER_BLOCK = MT / 32;
 
 __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     Ctl *ctl = b.ctl;
     if (input_failed(ctl)) return;   // decided before launch: uniform over the grid
     const u64 nc = min(ctl->n_cand, w.cand_cap);
+    // blocks in use (uniform: every block read the same count)
+    const unsigned nb = (unsigned)min((u64)gridDim.x, max((u64)1, (nc + MERGE_CANDS_PER_BLOCK - 1) / MERGE_CANDS_PER_BLOCK));
+    if (blockIdx.x >= nb) return;
+    const unsigned long long lim = b.spin_limit > 0 ? (unsigned long long)b.spin_limit : BARRIER_SPIN_LIMIT;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long nwarps = ((long long)nb * blockDim.x) >> 5;
     const u32 H = (u32)b.H;
     __shared__ int keep[MT / 32][32];   // per warp: undecided candidates waiting to be appended
     // candidates per window: at least 2^18, at most 128 windows, unless set
@@ -150,14 +131,14 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             ++my_active;
         }
         if (lane == 0 && my_active) atomicAdd(&ctl->active[round & 1], my_active);
-        if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
+        if (!coop_barrier(ctl->bar, nb, &ctl->error, ERRB_TIMEOUT, lim)) return;
         const u32 active = ld_cg_u32(&ctl->active[round & 1]);
         if (blockIdx.x == 0 && threadIdx.x == 0 && round < 64) ctl->round_active[round] = active;
         if (blockIdx.x == 0 && threadIdx.x == 0) ctl->active[(round + 1) & 1] = 0;
         if (active == 0) {   // the window is decided (uniform: every block read the same count)
             ++round;
             // the next window's first round counts into the counter just reset
-            if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
+            if (!coop_barrier(ctl->bar, nb, &ctl->error, ERRB_TIMEOUT, lim)) return;
             break;
         }
         // ---- phase 2: accept ready candidates, carry the others to the next round
@@ -255,7 +236,7 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
             if (lane < nkeep) next[pos + lane] = keep[wib][lane];
             __syncwarp();
         }
-        if (!grid_barrier(ctl, gridDim.x, b.spin_limit)) return;
+        if (!coop_barrier(ctl->bar, nb, &ctl->error, ERRB_TIMEOUT, lim)) return;
     }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
@@ -570,7 +551,7 @@ const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, 
     k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
     const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
                                          &b.ctl->n_cand, 3 * b.rbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
-                                         b.spin_limit);
+                                         b.ctl->bar, b.spin_limit);
     return o.sort_v[cur];
 }
 
@@ -589,23 +570,25 @@ void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, lon
     k_collect<<<g, 256, 0, st>>>(b, w, o);
     u64 *na = &b.ctl->n_acc;
     int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 3 * b.rbits,
-                                   temp, st, &b.ctl->error, ERRB_TIMEOUT, b.spin_limit);
+                                   temp, st, &b.ctl->error, ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
     if (b.V > 1) {
         k_view_keys<<<g, 256, 0, st>>>(b, w, o.sort_k[cur], o.sort_v[cur]);
         int c2 = radix_sort_pairs_dev(o.sort_k[cur], o.sort_v[cur], o.sort_k[cur ^ 1], o.sort_v[cur ^ 1], acc_cap,
                                       na, bits_for((unsigned long long)(b.V - 1)), temp, st, &b.ctl->error, ERRB_TIMEOUT,
-                                      b.spin_limit);
+                                      b.ctl->bar, b.spin_limit);
         cur = c2 ? (cur ^ 1) : cur;
     }
     cudaMemsetAsync(o.view_trk, 0, sizeof(long long) * (b.V + 1), st);
     k_track_meta<<<g, 256, 0, st>>>(b, w, o, o.sort_v[cur]);
-    exclusive_scan_u64_dev((const u64 *)o.view_trk, (u64 *)o.view_trk, b.V, nullptr, temp, nullptr, st);
-    exclusive_scan_u64_dev(o.trk_moff, o.trk_moff, acc_cap, na, temp, &b.ctl->n_out_members, st);
+    exclusive_scan_u64_dev((const u64 *)o.view_trk, (u64 *)o.view_trk, b.V, nullptr, temp, nullptr, st,
+                           &b.ctl->error, ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
+    exclusive_scan_u64_dev(o.trk_moff, o.trk_moff, acc_cap, na, temp, &b.ctl->n_out_members, st, &b.ctl->error,
+                           ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
     k_fit<<<g, 256, 0, st>>>(b, w, o);
     const int tbits = bits_for((unsigned long long)(acc_cap > 0 ? acc_cap : 1));
     int cm = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], out_member_cap,
                                   &b.ctl->n_out_members, b.rbits + tbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
-                                  b.spin_limit);
+                                  b.ctl->bar, b.spin_limit);
     k_members_out<<<g, 256, 0, st>>>(b, o, o.sort_k[cm]);
 }
 

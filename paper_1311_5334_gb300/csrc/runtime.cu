@@ -670,19 +670,21 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         launch_canonical_keys(b, keys[0], vals[0], st);
         const int kb = b.vshift + bits_for((unsigned long long)std::max(V - 1, 0));
         int c1 = radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], n, kb, temp, st, &ctl->error, ERRB_TIMEOUT,
-                                  b.spin_limit);
+                                  ctl->bar, b.spin_limit);
         u32 *sv = vals[c1], *cell_of = vals[c1 ^ 1];
         launch_canonical_order(b, keys[c1], sv, cell_of, cell_count, st);
         // cell list by counting sort: starts from the counts, then the counts
         // are zeroed and serve as per-cell cursors of the scatter
-        exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st);
+        exclusive_scan_u32(cell_count, cell_start, (long long)cells, temp, st, &ctl->error, ERRB_TIMEOUT, ctl->bar,
+                           b.spin_limit);
         cudaMemsetAsync(cell_count, 0, sizeof(u32) * cells, st);
         launch_cell_scatter(b, cell_of, cell_start, cell_count, 0, st);
         if (dual) {   // second cell list (rows along y) from the same canonical order
             const size_t cellsy = (size_t)V * (size_t)ncelly;
             cudaMemsetAsync(cell_count_y, 0, sizeof(u32) * cellsy, st);
             launch_y_cells(b, cell_of, cell_count_y, st);
-            exclusive_scan_u32(cell_count_y, cell_start_y, (long long)cellsy, temp, st);
+            exclusive_scan_u32(cell_count_y, cell_start_y, (long long)cellsy, temp, st, &ctl->error, ERRB_TIMEOUT,
+                               ctl->bar, b.spin_limit);
             cudaMemsetAsync(cell_count_y, 0, sizeof(u32) * cellsy, st);
             launch_cell_scatter(b, cell_of, cell_start_y, cell_count_y, 1, st);
         }
@@ -691,7 +693,8 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         launch_tube_count(b, w, record ? 1 : 0, st);
         mark(3, st);
         launch_cand_keys(b, w, st);
-        exclusive_scan_u64_dev(c_moff, c_moff, (long long)cap_cand, &ctl->n_cand, temp, &ctl->n_members, st);
+        exclusive_scan_u64_dev(c_moff, c_moff, (long long)cap_cand, &ctl->n_cand, temp, &ctl->n_members, st,
+                               &ctl->error, ERRB_TIMEOUT, ctl->bar, b.spin_limit);
         launch_member_fill(b, w, st);
         cudaMemsetAsync(best[0], 0xFF, sizeof(u64) * n, st);
         cudaMemsetAsync(best[1], 0xFF, sizeof(u64) * n, st);
@@ -967,6 +970,7 @@ et_status et_ctx_create(int device, et_ctx **out) {
     cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, device);
     cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
     c->merge_grid = merge_grid_blocks(device);
+    init_scan_sort();
     *out = c;
     return ET_OK;
     GUARD_END

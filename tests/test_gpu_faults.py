@@ -1,9 +1,9 @@
 """Failure handling without faulting the GPU: bounded device waits that run
 out, and the served loop's back-pressure and memory budget.
 
-The tuning knob wait_polls makes every bounded device-side wait (the
-association's grid barrier, the sorts' look-back) give up after that many
-polls.  A run with wait_polls = 1 must end with ET_ERR_TIMEOUT, a status the
+The tuning knob wait_polls makes every bounded device-side wait (the grid
+barriers of the association, the sorts and the scans; the sorts' look-back)
+give up after that many polls.  A run with wait_polls = 1 must end with ET_ERR_TIMEOUT, a status the
 host reads (no trap, no hang, the context stays usable), and the next run on
 the same batch with the default limit must equal the oracle.
 
@@ -27,7 +27,7 @@ def oracle_tuples(oracle_mod, v, p):
         o.close()
 
 
-def timeout_then_rerun(et, v, p):
+def timeout_then_rerun(et, v, p, cell=(0, 0, 0)):
     """Runs with wait_polls = 1 until a run times out (at most 3 tries), then
     once with the default limit on the same batch; returns (timeouts, tuples, stats)."""
     with et.Context(0) as ctx:
@@ -35,7 +35,7 @@ def timeout_then_rerun(et, v, p):
         try:
             timeouts = 0
             for _ in range(3):
-                b.set_tuning(wait_polls=1)
+                b.set_tuning(cell=cell, wait_polls=1)
                 b.load(v.xyz, [0, v.n])
                 b.find()
                 try:
@@ -44,7 +44,7 @@ def timeout_then_rerun(et, v, p):
                     assert e.status == et.TIMEOUT, e
                     timeouts += 1
                     break
-            b.set_tuning()
+            b.set_tuning(cell=cell)
             b.load(v.xyz, [0, v.n])
             b.find()
             tracks, members, _ = b.fetch()
@@ -55,20 +55,24 @@ def timeout_then_rerun(et, v, p):
 
 
 def test_association_barrier_wait_runs_out(oracle_mod):
-    """A view whose sorts all fit one tile (no look-back waits): the only
-    device wait is the grid barrier between association rounds."""
+    """A small view on 15 x 15 x 15 cells: every sort and scan fits one tile,
+    so one block does it with no wait, and the association keeps more than
+    one block (over 32 candidates).  The only device wait is the grid barrier
+    between association rounds."""
     from paper_1311_5334_gb300 import et
     v = synth.make_view(31, n_fog=1000, n_through=10)
     p = synth.params(v.extent)
-    timeouts, got, st = timeout_then_rerun(et, v, p)
-    assert v.n < 2048 and 0 < st["n_candidates"] < 2048, (v.n, st["n_candidates"])
+    cell = tuple(-(-e // 15) for e in v.extent)
+    timeouts, got, st = timeout_then_rerun(et, v, p, cell)
+    assert v.n < 2048 and 32 < st["n_candidates"] < 2048, (v.n, st["n_candidates"])
     assert timeouts == 1
     assert got == oracle_tuples(oracle_mod, v, p)
 
 
 def test_sort_lookback_wait_runs_out(oracle_mod):
-    """The dense view (15 tiles in the first sort): the look-back of a tile
-    on its predecessor gives up after one poll."""
+    """The dense view (15 tiles in the first sort): a tile's look-back on its
+    predecessor, or a grid barrier between the sort's passes, gives up after
+    one poll."""
     from paper_1311_5334_gb300 import et
     v = synth.dense()
     p = synth.params(v.extent)
