@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "et.h"   // ET_FLAG_* variant bits
 
 namespace et {
@@ -188,6 +190,32 @@ __device__ __forceinline__ bool coop_barrier(u32 *bar, unsigned nblocks, u32 *er
     return (*(volatile u32 *)err & err_bit) == 0;
 }
 
+// Programmatic dependent launch.  A kernel launched by launch_dep may be
+// scheduled while the kernel before it on the stream is still running (that
+// one lets it by griddep_launch at its start); griddep_wait, the first
+// statement of every such kernel, then holds it until the kernel before has
+// completed and its memory writes are visible.  The overlap hides the
+// launch and block start-up of short kernels.  Cooperative launches keep a
+// plain stream dependency, so their blocks never compete with waiting ones.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline cudaError_t launch_dep(void (*fn)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
 // Blocks of a cooperative launch of kernel fn with the given block size that
 // fit on the device at once (0 if the query fails).
 template <class F>
@@ -244,9 +272,11 @@ void launch_y_cells(const Batch &b, u32 *cell_of, u32 *cell_count, cudaStream_t 
 
 // count.cu
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st);
-void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st);
+// sort_k / sort_v: input of the candidate-order sort (null: not written)
+void launch_cand_keys(const Batch &b, const Work &w, u64 *sort_k, u32 *sort_v, cudaStream_t st);
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st);
 void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st);
+// candidates in key order, from the sort input written by launch_cand_keys
 const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st);
 
 // merge.cu

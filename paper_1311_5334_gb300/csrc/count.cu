@@ -559,6 +559,8 @@ __device__ __forceinline__ bool gen_pass(const Batch &b, GenSm<SG> &sm, GenState
 
 template <int SG>
 __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int record) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     __shared__ SeedTab sp[TW];
     __shared__ int4 tbl[TW][32];
@@ -648,7 +650,11 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
 
 // Candidate keys: (2^21 - 1 - count) << 42 | rank_lo << 21 | rank_hi, so that
 // ascending keys visit candidates by count descending, then ranks ascending.
-__global__ void k_cand_keys(Batch b, Work w) {
+// With sk not null, also the input of the candidate-order sort: the key on
+// 3 * rbits bits and the candidate index.
+__global__ void k_cand_keys(Batch b, Work w, u64 *sk, u32 *sv) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -657,9 +663,14 @@ __global__ void k_cand_keys(Batch b, Work w) {
         const int v = view_of(b.goff, b.V, lo);
         const u64 rlo = (u64)(lo - b.goff[v]), rhi = (u64)(hi - b.goff[v]);
         const u64 cnt = w.c_cnt[c];
-        w.c_key[c] = ((((1ull << 21) - 1ull) - cnt) << 42) | (rlo << 21) | rhi;
+        const u64 key = ((((1ull << 21) - 1ull) - cnt) << 42) | (rlo << 21) | rhi;
+        w.c_key[c] = key;
         w.c_moff[c] = cnt;
         w.c_state[c] = CS_UNDECIDED;
+        if (sk) {
+            sk[c] = cand_sort_key(b, key);
+            sv[c] = (u32)c;
+        }
     }
 }
 
@@ -667,6 +678,8 @@ __global__ void k_cand_keys(Batch b, Work w) {
 // each in-tube grain takes the next slot of its candidate's member range
 // (a shared-memory cursor), so the order inside a list is arbitrary.
 __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     if (b.ctl->n_members > w.member_cap) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&b.ctl->error, ERRB_OVF_MEMBERS);
@@ -721,17 +734,17 @@ unsigned persistent_grid(int blocks_per_sm) {
 }  // namespace
 
 void launch_tube_count(const Batch &b, const Work &w, int record, cudaStream_t st) {
-    if (b.gen_origins == 1) k_tube_count<1><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
-    else if (b.gen_origins == 4) k_tube_count<4><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
-    else k_tube_count<2><<<persistent_grid(8), TW * 32, 0, st>>>(b, w, record);
+    if (b.gen_origins == 1) launch_dep(k_tube_count<1>, dim3(persistent_grid(8)), dim3(TW * 32), 0, st, b, w, record);
+    else if (b.gen_origins == 4) launch_dep(k_tube_count<4>, dim3(persistent_grid(8)), dim3(TW * 32), 0, st, b, w, record);
+    else launch_dep(k_tube_count<2>, dim3(persistent_grid(8)), dim3(TW * 32), 0, st, b, w, record);
 }
 
-void launch_cand_keys(const Batch &b, const Work &w, cudaStream_t st) {
-    k_cand_keys<<<persistent_grid(4), 256, 0, st>>>(b, w);
+void launch_cand_keys(const Batch &b, const Work &w, u64 *sort_k, u32 *sort_v, cudaStream_t st) {
+    launch_dep(k_cand_keys, dim3(persistent_grid(4)), dim3(256), 0, st, b, w, sort_k, sort_v);
 }
 
 void launch_member_fill(const Batch &b, const Work &w, cudaStream_t st) {
-    k_member_fill<<<persistent_grid(8), TW * 32, 0, st>>>(b, w);
+    launch_dep(k_member_fill, dim3(persistent_grid(8)), dim3(TW * 32), 0, st, b, w);
 }
 
 }  // namespace et

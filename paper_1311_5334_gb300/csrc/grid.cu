@@ -18,6 +18,8 @@ namespace et {
 namespace {
 
 __global__ void k_canonical_keys(Batch b, u64 *keys, u32 *vals) {
+    griddep_launch();
+    griddep_wait();
     const long long stride = (long long)gridDim.x * blockDim.x;
     const int sy = b.cbits[2], sx = b.cbits[1] + b.cbits[2];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < b.N; i += stride) {
@@ -37,6 +39,8 @@ __global__ void k_canonical_keys(Batch b, u64 *keys, u32 *vals) {
 
 __global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u32 *cell_of,
                                   u32 *cell_count) {
+    griddep_launch();
+    griddep_wait();
     // a coordinate out of range is reported as such; a timed-out sort leaves
     // invalid indices: either way nothing after this point may run
     if (input_failed(b.ctl)) return;
@@ -63,6 +67,8 @@ __global__ void k_canonical_order(Batch b, const u64 *keys, const u32 *vals, u32
 // slot of its cell (cursor zeroed before the launch).
 __global__ void k_cell_scatter(Batch b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int4 *gc,
                                u64 *gp) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
@@ -76,6 +82,8 @@ __global__ void k_cell_scatter(Batch b, const u32 *cell_of, const u32 *cell_star
 
 // Cells of the second cell list (rows along y) for the canonical order.
 __global__ void k_y_cells(Batch b, u32 *cell_of, u32 *cell_count) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < b.N; p += stride) {
@@ -100,22 +108,22 @@ unsigned grid_for(long long n, int threads) {
 }  // namespace
 
 void launch_canonical_keys(const Batch &b, u64 *keys, u32 *vals, cudaStream_t st) {
-    k_canonical_keys<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals);
+    launch_dep(k_canonical_keys, dim3(grid_for(b.N, 256)), dim3(256), 0, st, b, keys, vals);
 }
 
 void launch_canonical_order(const Batch &b, const u64 *keys, const u32 *vals, u32 *cell_of, u32 *cell_count,
                             cudaStream_t st) {
-    k_canonical_order<<<grid_for(b.N, 256), 256, 0, st>>>(b, keys, vals, cell_of, cell_count);
+    launch_dep(k_canonical_order, dim3(grid_for(b.N, 256)), dim3(256), 0, st, b, keys, vals, cell_of, cell_count);
 }
 
 void launch_cell_scatter(const Batch &b, const u32 *cell_of, const u32 *cell_start, u32 *cursor, int ylist,
                          cudaStream_t st) {
-    k_cell_scatter<<<grid_for(b.N, 256), 256, 0, st>>>(b, cell_of, cell_start, cursor, ylist ? b.gcy : b.gc,
+    launch_dep(k_cell_scatter, dim3(grid_for(b.N, 256)), dim3(256), 0, st, b, cell_of, cell_start, cursor, ylist ? b.gcy : b.gc,
                                                        ylist ? b.gpy : b.gp);
 }
 
 void launch_y_cells(const Batch &b, u32 *cell_of, u32 *cell_count, cudaStream_t st) {
-    k_y_cells<<<grid_for(b.N, 256), 256, 0, st>>>(b, cell_of, cell_count);
+    launch_dep(k_y_cells, dim3(grid_for(b.N, 256)), dim3(256), 0, st, b, cell_of, cell_count);
 }
 
 }  // namespace et

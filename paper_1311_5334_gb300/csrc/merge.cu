@@ -60,6 +60,8 @@ __device__ __forceinline__ u32 ld_cg_u32(const u32 *p) { return __ldcg(p); }
 constexpr u64 MERGE_CANDS_PER_BLOCK = MT / 32;
 
 __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
+    griddep_launch();
+    griddep_wait();
     Ctl *ctl = b.ctl;
     if (input_failed(ctl)) return;   // decided before launch: uniform over the grid
     const u64 nc = min(ctl->n_cand, w.cand_cap);
@@ -242,17 +244,6 @@ __global__ void __launch_bounds__(MT) k_merge(Batch b, Work w) {
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->rounds = round;
 }
 
-// Candidate keys and indices, sorted by key (the association's windows).
-__global__ void k_cand_sort_in(Batch b, Work w, u64 *k, u32 *v) {
-    if (input_failed(b.ctl)) return;
-    const u64 nc = min(b.ctl->n_cand, w.cand_cap);
-    const u64 stride = (u64)gridDim.x * blockDim.x;
-    for (u64 c = (u64)blockIdx.x * blockDim.x + threadIdx.x; c < nc; c += stride) {
-        k[c] = cand_sort_key(b, w.c_key[c]);
-        v[c] = (u32)c;
-    }
-}
-
 // Angle cut (ET_FLAG_ANGLE_CUT): keep a track iff
 //     nhits >= cut_base + cut_slope * min(tan theta, cut_tmax),
 // tan theta = sqrt(wx^2 + wy^2) / |wz| for the seed vector w, in exact
@@ -273,6 +264,8 @@ __device__ __forceinline__ bool angle_cut_keeps(const Batch &b, int4 glo, int4 g
 // Single-pass association (ET_FLAG_SINGLE_PASS), step 1: every grain keeps the
 // smallest key of the candidates whose tube holds it (one warp per candidate).
 __global__ void k_sp_best(Batch b, Work w) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     const int lane = threadIdx.x & 31;
@@ -286,6 +279,8 @@ __global__ void k_sp_best(Batch b, Work w) {
 // Step 2: a candidate owns the grains whose smallest key is its own; it is a
 // track iff it owns at least min_hits of them.
 __global__ void k_sp_own(Batch b, Work w) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     const int lane = threadIdx.x & 31;
@@ -310,6 +305,8 @@ __global__ void k_sp_own(Batch b, Work w) {
 
 // Accepted candidates -> list (any order) with sort keys.
 __global__ void k_collect(Batch b, Work w, Out o) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 nc = min(b.ctl->n_cand, w.cand_cap);
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -325,6 +322,8 @@ __global__ void k_collect(Batch b, Work w, Out o) {
 
 // After the key sort: second key = view (stable sort keeps key order).
 __global__ void k_view_keys(Batch b, Work w, u64 *k, const u32 *v) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;   // a timed-out sort leaves invalid indices
     const u64 na = b.ctl->n_acc;
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -332,8 +331,11 @@ __global__ void k_view_keys(Batch b, Work w, u64 *k, const u32 *v) {
         k[i] = (u64)view_of(b.goff, b.V, w.c_lo[v[i]]);
 }
 
-// Sorted accepted list -> per-track view, nhits (for the member scan) and per-view counts.
+// Sorted accepted list -> per-track view, nhits (for the member scan) and
+// per-view counts (with one view, the view's track offsets).
 __global__ void k_track_meta(Batch b, Work w, Out o, const u32 *sorted_c) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 na = b.ctl->n_acc;
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -343,7 +345,11 @@ __global__ void k_track_meta(Batch b, Work w, Out o, const u32 *sorted_c) {
         const int v = view_of(b.goff, b.V, w.c_lo[c]);
         o.trk_view[t] = v;
         o.trk_moff[t] = w.c_nfree[c];
-        atomicAdd((unsigned long long *)&o.view_trk[v], 1ull);
+        if (b.V > 1) atomicAdd((unsigned long long *)&o.view_trk[v], 1ull);
+    }
+    if (b.V == 1 && blockIdx.x == 0 && threadIdx.x == 0) {   // one view: its track offsets directly
+        o.view_trk[0] = 0;
+        o.view_trk[1] = (long long)na;
     }
 }
 
@@ -400,6 +406,8 @@ __device__ void jacobi3f(float A[3][3], float V[3][3]) {
 // One warp per accepted track: exact integer moments about the lo seed grain,
 // FP32 principal axis, member projections; member keys for the final sort.
 __global__ void k_fit(Batch b, Work w, Out o) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 na = b.ctl->n_acc;
     const int lane = threadIdx.x & 31;
@@ -505,6 +513,8 @@ __global__ void k_fit(Batch b, Work w, Out o) {
 }
 
 __global__ void k_members_out(Batch b, Out o, const u64 *sorted_k) {
+    griddep_launch();
+    griddep_wait();
     if (input_failed(b.ctl)) return;
     const u64 nm = b.ctl->n_out_members;
     const u64 stride = (u64)gridDim.x * blockDim.x;
@@ -548,7 +558,6 @@ cudaError_t launch_merge_coop(const Batch &b, const Work &w, int grid, cudaStrea
 }
 
 const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, cudaStream_t st) {
-    k_cand_sort_in<<<sm_count() * 4, 256, 0, st>>>(b, w, o.sort_k[0], o.sort_v[0]);
     const int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], (long long)o.acc_cap,
                                          &b.ctl->n_cand, 3 * b.rbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
                                          b.ctl->bar, b.spin_limit);
@@ -557,8 +566,8 @@ const u32 *launch_cand_order(const Batch &b, const Work &w, Out &o, void *temp, 
 
 void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st) {
     const unsigned g = sm_count() * 8;
-    k_sp_best<<<g, 256, 0, st>>>(b, w);
-    k_sp_own<<<g, 256, 0, st>>>(b, w);
+    launch_dep(k_sp_best, dim3(g), dim3(256), 0, st, b, w);
+    launch_dep(k_sp_own, dim3(g), dim3(256), 0, st, b, w);
 }
 
 // Accepted list sorted by (view, key); per-view track offsets; member offsets;
@@ -567,29 +576,30 @@ void launch_single_pass(const Batch &b, const Work &w, cudaStream_t st) {
 void launch_output(const Batch &b, const Work &w, Out &o, long long acc_cap, long long out_member_cap,
                    void *temp, cudaStream_t st) {
     const unsigned g = sm_count() * 4;
-    k_collect<<<g, 256, 0, st>>>(b, w, o);
+    launch_dep(k_collect, dim3(g), dim3(256), 0, st, b, w, o);
     u64 *na = &b.ctl->n_acc;
     int cur = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], acc_cap, na, 3 * b.rbits,
                                    temp, st, &b.ctl->error, ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
     if (b.V > 1) {
-        k_view_keys<<<g, 256, 0, st>>>(b, w, o.sort_k[cur], o.sort_v[cur]);
+        launch_dep(k_view_keys, dim3(g), dim3(256), 0, st, b, w, o.sort_k[cur], o.sort_v[cur]);
         int c2 = radix_sort_pairs_dev(o.sort_k[cur], o.sort_v[cur], o.sort_k[cur ^ 1], o.sort_v[cur ^ 1], acc_cap,
                                       na, bits_for((unsigned long long)(b.V - 1)), temp, st, &b.ctl->error, ERRB_TIMEOUT,
                                       b.ctl->bar, b.spin_limit);
         cur = c2 ? (cur ^ 1) : cur;
     }
-    cudaMemsetAsync(o.view_trk, 0, sizeof(long long) * (b.V + 1), st);
-    k_track_meta<<<g, 256, 0, st>>>(b, w, o, o.sort_v[cur]);
-    exclusive_scan_u64_dev((const u64 *)o.view_trk, (u64 *)o.view_trk, b.V, nullptr, temp, nullptr, st,
-                           &b.ctl->error, ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
+    if (b.V > 1) cudaMemsetAsync(o.view_trk, 0, sizeof(long long) * (b.V + 1), st);
+    launch_dep(k_track_meta, dim3(g), dim3(256), 0, st, b, w, o, o.sort_v[cur]);
+    if (b.V > 1)
+        exclusive_scan_u64_dev((const u64 *)o.view_trk, (u64 *)o.view_trk, b.V, nullptr, temp, nullptr, st,
+                               &b.ctl->error, ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
     exclusive_scan_u64_dev(o.trk_moff, o.trk_moff, acc_cap, na, temp, &b.ctl->n_out_members, st, &b.ctl->error,
                            ERRB_TIMEOUT, b.ctl->bar, b.spin_limit);
-    k_fit<<<g, 256, 0, st>>>(b, w, o);
+    launch_dep(k_fit, dim3(g), dim3(256), 0, st, b, w, o);
     const int tbits = bits_for((unsigned long long)(acc_cap > 0 ? acc_cap : 1));
     int cm = radix_sort_pairs_dev(o.sort_k[0], o.sort_v[0], o.sort_k[1], o.sort_v[1], out_member_cap,
                                   &b.ctl->n_out_members, b.rbits + tbits, temp, st, &b.ctl->error, ERRB_TIMEOUT,
                                   b.ctl->bar, b.spin_limit);
-    k_members_out<<<g, 256, 0, st>>>(b, o, o.sort_k[cm]);
+    launch_dep(k_members_out, dim3(g), dim3(256), 0, st, b, o, o.sort_k[cm]);
 }
 
 }  // namespace et

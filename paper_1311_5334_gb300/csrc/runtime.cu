@@ -692,7 +692,8 @@ et_status BatchRT::enqueue(cudaStream_t st, bool record) {
         mark(2, st);
         launch_tube_count(b, w, record ? 1 : 0, st);
         mark(3, st);
-        launch_cand_keys(b, w, st);
+        const bool sp = (p.flags & ET_FLAG_SINGLE_PASS) != 0;
+        launch_cand_keys(b, w, sp ? nullptr : o.sort_k[0], sp ? nullptr : o.sort_v[0], st);
         exclusive_scan_u64_dev(c_moff, c_moff, (long long)cap_cand, &ctl->n_cand, temp, &ctl->n_members, st,
                                &ctl->error, ERRB_TIMEOUT, ctl->bar, b.spin_limit);
         launch_member_fill(b, w, st);

@@ -85,6 +85,8 @@ template <class T>
 __global__ void __launch_bounds__(SC_T) k_scan(const T *in, T *out, long long n_cap, const u64 *n_dev, T *partial,
                                                u64 *total_out, u32 *bar, u32 *err, u32 err_bit,
                                                unsigned long long lim) {
+    griddep_launch();
+    griddep_wait();
     if (*(volatile u32 *)err & err_bit) return;
     const long long n = eff_n(n_cap, n_dev);
     const long long nt = n > 0 ? (n + SC_TILE - 1) / SC_TILE : 1;
@@ -340,6 +342,8 @@ constexpr size_t rss_smem() {
 template <int NT>
 __global__ void __launch_bounds__(NT, 1) k_rs_small(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap,
                                                     const u64 *n_dev, int npass, u32 *err, u32 err_bit) {
+    griddep_launch();
+    griddep_wait();
     extern __shared__ __align__(16) unsigned char rss_smem_buf[];
     if (*(volatile u32 *)err & err_bit) return;
     const int n = (int)eff_n(n_cap, n_dev);
@@ -352,6 +356,8 @@ __global__ void __launch_bounds__(NT, 1) k_rs_small(u64 *k0, u32 *v0, u64 *k1, u
 __global__ void __launch_bounds__(RS_T, 4) k_rs_sort(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap,
                                                   const u64 *n_dev, int npass, RsTemp tp, u32 *bar, u32 *err,
                                                   u32 err_bit, unsigned long long lim) {
+    griddep_launch();
+    griddep_wait();
     struct Tiles {   // the tiled passes
         u32 base[RS_MAXP][256];   // the block's histogram, then per-pass digit offsets
         u32 wcnt[RS_W][256];      // per warp and digit: count, then output position
@@ -555,11 +561,11 @@ int radix_sort_pairs_dev(u64 *k0, u32 *v0, u64 *k1, u32 *v1, long long n_cap, co
     if (ntiles == 0 || npass == 0) return 0;
     if (n_cap <= RSS_MAX) {   // a short list by capacity: one block, every pass on chip
         if (n_cap <= 256 * 8)
-            k_rs_small<256><<<1, 256, rss_smem<256>(), st>>>(k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
+            launch_dep(k_rs_small<256>, dim3(1), dim3(256), rss_smem<256>(), st, k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
         else if (n_cap <= 512 * 8)
-            k_rs_small<512><<<1, 512, rss_smem<512>(), st>>>(k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
+            launch_dep(k_rs_small<512>, dim3(1), dim3(512), rss_smem<512>(), st, k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
         else
-            k_rs_small<1024><<<1, 1024, rss_smem<1024>(), st>>>(k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
+            launch_dep(k_rs_small<1024>, dim3(1), dim3(1024), rss_smem<1024>(), st, k0, v0, k1, v1, n_cap, n_dev, npass, err, err_bit);
         return npass & 1;
     }
     RsTemp tp;
