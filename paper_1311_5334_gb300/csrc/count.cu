@@ -210,6 +210,12 @@ __device__ __forceinline__ int4 grain_at(const Batch &b, u32 k) {
     return b.gc[k];
 }
 
+// Grains of its own rows a lane tests itself before the rest is dealt (1 was
+// the fastest of 0, 1, 2, 3, 4 and 6 on the batched, dense, PR1 and stress
+// workloads: the lane's own loads touch up to 32 lines per warp load, so more
+// than one costs more than dealing them).
+constexpr int WALK_SERIAL = 1;
+
 // Adds 1 to a shared-memory counter when p holds, without a branch.
 __device__ __forceinline__ void red_add_if(bool p, u32 *addr) {
     const unsigned a = (unsigned)__cvta_generic_to_shared(addr);
@@ -220,7 +226,7 @@ __device__ __forceinline__ void red_add_if(bool p, u32 *addr) {
 
 // COUNT: in the dealt passes every grain inside the tube of line s adds 1 to
 // cnt[s] by a predicated reduction; otherwise hit(s, g) is called for it.
-template <bool PACKED, bool COUNT, class Hit>
+template <bool PACKED, bool COUNT, int SERIAL, class Hit>
 __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tbl, int n_items, u32 &tests,
                                            u32 *cnt, Hit &&hit) {
     const int lane = threadIdx.x & 31;
@@ -321,9 +327,34 @@ __device__ __forceinline__ void warp_items(const Batch &b, SeedTab &sp, int4 *tb
                 }
             }
         }
-        // deal the grains of all lanes' first two rows over the warp
+        tests += n0 + n1;
+        if (SERIAL > 0 && __any_sync(0xffffffffu, n0 + n1 > 0)) {
+            // the first SERIAL grains of its rows each lane tests itself, with its
+            // line's parameters in registers (cheaper per test than dealing);
+            // only the grains beyond them are dealt over the warp
+            const u32 s0 = min(n0, (u32)SERIAL), s1 = min(n1, (u32)SERIAL - s0);
+            if (s0 + s1 > 0) {
+                const int4 e0 = sp.i4(0, own), e1 = sp.i4(1, own);
+                const long long R = (long long)(((unsigned long long)(unsigned)e1.w << 32) | (unsigned)e1.z);
+                const int3 a = make_int3(e0.x, e0.y, e0.z), d = make_int3(e0.w, e1.x, e1.y);
+#pragma unroll
+                for (int j = 0; j < SERIAL; ++j) {
+                    if ((u32)j < s0 + s1) {
+                        const u32 k = loff + ((u32)j < s0 ? b0 + (u32)j : b1 + ((u32)j - s0));
+                        const int4 g = grain_at<PACKED>(b, k);
+                        const bool h = in_tube(g, a, d, R);
+                        if (COUNT) red_add_if(h, &cnt[own]);
+                        else if (h) hit(own, g);
+                    }
+                }
+            }
+            b0 += s0;
+            n0 -= s0;
+            b1 += s1;
+            n1 -= s1;
+        }
+        // deal the remaining grains of all lanes' first two rows over the warp
         const u32 n = n0 + n1;
-        tests += n;
         u32 rin = n;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -597,7 +628,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_tube_count(Batch b, Work w, int 
         }
         scount[wib][lane] = 0;
         __syncwarp();
-        warp_items<true, true>(b, sp[wib], tbl[wib], n_items, tests, scount[wib],
+        warp_items<true, true, WALK_SERIAL>(b, sp[wib], tbl[wib], n_items, tests, scount[wib],
                                [&](int own, int4) { atomicAdd(&scount[wib][own], 1u); });
         __syncwarp();
         const u32 count = valid ? scount[wib][lane] : 0u;
@@ -712,7 +743,7 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
         }
         __syncwarp();
         u32 tests = 0;
-        warp_items<false, false>(b, sp[wib], tbl[wib], n_items, tests, cursor[wib], [&](int own, int4 g) {
+        warp_items<false, false, WALK_SERIAL>(b, sp[wib], tbl[wib], n_items, tests, cursor[wib], [&](int own, int4 g) {
             members[mbase[wib][own] + atomicAdd(&cursor[wib][own], 1u)] = g.w;
         });
         __syncwarp();
