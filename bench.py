@@ -49,11 +49,11 @@ OPS_PER_PAIR_TEST = 6
 # counts) moves, dram__bytes_read.sum + dram__bytes_write.sum of one ncu
 # capture of that launch (one pass, the first timed step, the kernel as built
 # now; profiles/k_tube_count_batched.md):
-#   batched  613.30 MB + 45.13 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
+#   batched  613.92 MB + 45.33 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
 # The kernel reads each view's grains and cell tables about once, so the bytes
 # follow the views and the cell shape rather than the seeds; workloads without
 # a capture of their own launch report null.
-TUBE_DRAM_BYTES = {"batched": 613.30e6 + 45.13e6}
+TUBE_DRAM_BYTES = {"batched": 613.92e6 + 45.33e6}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
