@@ -279,7 +279,7 @@ def run_ours(args):
     tuned = None
     if args.cell:
         batch.set_tuning(tuple(int(c) for c in args.cell.split(",")), row_lists=args.rows,
-                         ticket_origins=args.ticket_origins)
+                         ticket_origins=args.ticket_origins, assoc_window=args.assoc_window)
     batch.load(xyz_d, offs, stream=stream)
     if not args.cell:
         cell, ms = batch.autotune(stream=stream)
@@ -857,6 +857,8 @@ def main():
     ap.add_argument("--rows", type=int, default=1, help="with --cell: 1 = x-row cell list, 2 = x and y rows")
     ap.add_argument("--ticket-origins", type=int, default=0,
                     help="with --cell: seed origins per work ticket (1, 2 or 4; 0 = automatic)")
+    ap.add_argument("--assoc-window", type=int, default=0,
+                    help="with --cell: candidates per association window (0 = automatic)")
     ap.add_argument("--served-views", type=int, default=10000,
                     help="distinct views of the served sweep (one run per rate of 100..5000 views/s)")
     ap.add_argument("--flags", type=int, default=0,
