@@ -1,12 +1,14 @@
-"""The allocation-free entry point (et_tube_count_noalloc) against the oracle.
+"""The allocation-free entry point (et_tube_count_noalloc) against the oracle
+and against the regular, allocating path's per-seed counts.
 
 It serves callers that cannot allocate device memory: an acquisition loop
 that must not block on an allocation's device-wide synchronisation, code in a
 host function enqueued on a stream, or a process whose framework owns the free
 device memory.  The entry point keeps its cell list in one fixed device array
 shared by all calls, so each test makes two calls in a row on the same stream
-and checks both results against the CPU oracle's exact counts: the second call
-must not see anything the first one left behind.  It lives in its own file,
+and checks both results against the CPU oracle's exact counts (and, for the
+seeds of a view, against et_view_seed_counts of the regular path): the second
+call must not see anything the first one left behind.  It lives in its own file,
 collected last, so that a run stopping at the first failure has already run
 every other test.
 """
@@ -66,7 +68,23 @@ def test_noalloc_counts_match_oracle_on_two_calls(oracle_mod):
     pairs = np.concatenate([np.stack([lo, hi], 1), extra])
     want, bad = _expected(oracle_mod, v.xyz, p, pairs)
     assert bad[-3:].all() and not bad[:-3].any()
+    # the regular, allocating path's per-seed table for the same view
+    # (et_view_seed_counts after et_track_find), keyed by the seed's grain ids
+    with et.Context(0) as ctx:
+        view = ctx.view(v.xyz, p)
+        view.find()
+        view.fetch()
+        si, sj, sc = view.seed_counts()
+        view.close()
+    n = len(v.xyz)
+    order = np.argsort(si.astype(np.int64) * n + sj)
+    keys = (si.astype(np.int64) * n + sj)[order]
+    pos = np.searchsorted(keys, lo.astype(np.int64) * n + hi)
+    assert len(si) == len(lo) and np.array_equal(keys[pos], lo.astype(np.int64) * n + hi)
+    regular = sc[order][pos]
+    assert np.array_equal(regular, want[:len(lo)]), "regular path differs from the oracle"
     for call, got in enumerate(_noalloc_twice(et, torch, v.xyz, p, pairs)):
+        assert np.array_equal(got[:len(lo)], regular), f"call {call}: differs from et_view_seed_counts"
         assert np.array_equal(got, want), f"call {call}"
 
 
