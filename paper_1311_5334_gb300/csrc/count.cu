@@ -723,17 +723,23 @@ __global__ void __launch_bounds__(TW * 32, 4) k_member_fill(Batch b, Work w) {
     __shared__ unsigned long long mbase[TW][32];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *__restrict__ members = w.members;
-    const u64 tsize = ticket_size(nc);
+    // lines walked together by a warp: 32, or fewer (at least 4) when the
+    // candidates cannot give every warp of the grid 32; the rounds a warp
+    // walks in sequence, not the work, then set the kernel's duration
+    const u64 nwarps = (u64)gridDim.x * TW;
+    const u64 per_warp = (nc + nwarps - 1) / nwarps;
+    const int lines = per_warp >= 32 ? 32 : (per_warp < 4 ? 4 : (int)per_warp);
+    const u64 tsize = lines == 32 ? ticket_size(nc) : (u64)lines;
     for (;;) {
     u64 c0 = 0;
     if (lane == 0) c0 = atomicAdd(&b.ctl->ticket[1], tsize);
     c0 = __shfl_sync(0xffffffffu, c0, 0);
     if (c0 >= nc) break;
     const u64 c1 = min(c0 + tsize, nc);
-    for (u64 base = c0; base < c1; base += 32) {
+    for (u64 base = c0; base < c1; base += (u64)lines) {
         const u64 c = base + lane;
         int n_items = 0;
-        if (c < c1) {
+        if (lane < lines && c < c1) {
             const int lo = __ldcs(&w.c_lo[c]), hi = __ldcs(&w.c_hi[c]);
             SeedSm q;
             n_items = seed_setup(b, b.gr[lo], b.gr[hi], view_of(b.goff, b.V, lo), q);
