@@ -51,9 +51,42 @@ OPS_PER_PAIR_TEST = 6
 # now; profiles/k_tube_count_batched.md):
 #   batched  613.92 MB + 45.33 MB  (256 views, cells 74x621x506, both lists, 2 origins per ticket)
 # The kernel reads each view's grains and cell tables about once, so the bytes
-# follow the views and the cell shape rather than the seeds; workloads without
-# a capture of their own launch report null.
-TUBE_DRAM_BYTES = {"batched": 613.92e6 + 45.33e6}
+# follow the views and the cell shape rather than the seeds.  Keyed by
+# (workload, views, cell edges, cell lists, origins per ticket); a run under
+# any other launch configuration reports null.
+TUBE_DRAM_BYTES = {("batched", 256, (74, 621, 506), 2, 2): 613.92e6 + 45.33e6}
+
+
+def tube_run_key(workload, n_views, cell, tuning, rows=1, ticket_origins=0):
+    """Launch configuration of a tracking run, the key of TUBE_DRAM_BYTES:
+    (workload, views, cell edges, cell lists, seed origins per ticket).
+    tuning: the autotuner's choice, or None for edges fixed on the command
+    line (rows 1 = x rows only, else both lists; 0 origins = the default 2)."""
+    if tuning is not None:
+        lists, origins = int(tuning["row_lists"]), int(tuning["ticket_origins"])
+    else:
+        lists, origins = (1 if rows == 1 else 2), (int(ticket_origins) or 2)
+    return (workload, int(n_views), tuple(int(c) for c in cell), lists, origins)
+
+
+def hbm_roofline(traffic, kernel_ms, peaks):
+    """DRAM bytes of one launch over its kernel time against the measured copy
+    bandwidth; None without a traffic capture for the launch configuration."""
+    if traffic is None:
+        return None
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = traffic / (kernel_ms / 1e3) / 1e9
+    return {"traffic_bytes": traffic, "achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak,
+            "peak_src": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+
+
+def measured_peaks():
+    """The measured peaks (MEASURED_PEAKS.json), or {} when absent."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 # DRAM bytes of the front end's recognition kernel per view of raw frames
 # (dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of 8 views:
 # 430.69 MB + 6.07 MB); a launch's traffic is scaled by its view count.
@@ -334,6 +367,13 @@ def run_ours(args):
     achieved_tube = ops_tube / (tube_avg_ms / 1e3) / 1e12
     peak = info["sm_count"] * 128 * 2070e6 / 1e12
     stage_ms = ref_stats["stage_ms"]
+    # DRAM bytes of one tube-count launch (an ncu capture of this launch
+    # configuration) over the same in-graph kernel time, against the measured
+    # copy bandwidth: how far the kernel is from being bound by HBM
+    run_key = tube_run_key(args.workload, n_views, ref_stats["cell"], batch.tuning if tuned else None,
+                           rows=args.rows, ticket_origins=args.ticket_origins)
+    traffic = TUBE_DRAM_BYTES.get(run_key)
+    hbm = hbm_roofline(traffic, tube_avg_ms, measured_peaks())
 
     line_extra = {}
     if args.no_extra:
@@ -371,7 +411,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": "k_tube_count", "achieved": achieved, "peak": peak,
                          "unit": "Tops/s", "frac": achieved / peak,
                          "frac_tube_tests_only": achieved_tube / peak,
-                         "traffic": TUBE_DRAM_BYTES.get(args.workload),
+                         "traffic": traffic, "hbm": hbm,
                          "basis": f"({OPS_PER_TEST} int ops per tube test x {ref_stats['n_tests']} tests + "
                                   f"{OPS_PER_PAIR_TEST} per seed-window test x {ref_stats['n_pair_tests']} "
                                   f"window tests of the seed generator) / {tube_avg_ms:.3f} ms (in-graph "
@@ -745,12 +785,7 @@ def run_frames(args):
     k_ms = float(np.mean(kern_ms))
     alg_bytes = V * view_bytes + 3 * H * W + 28 * ref["n_grains"]
     achieved = alg_bytes / (k_ms / 1e3) / 1e9
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except OSError:
-        pass
+    peaks = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
 

@@ -31,3 +31,25 @@ def test_reference_arm_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_tube_traffic_applies_only_to_its_launch_configuration():
+    """The ncu traffic of the tube-count launch is reported only for the launch
+    configuration it was captured on, and its HBM fraction is bytes over the
+    kernel time against the measured copy bandwidth."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cap = bench.tube_run_key("batched", 256, [74, 621, 506], None, rows=2, ticket_origins=2)
+    assert cap in bench.TUBE_DRAM_BYTES
+    tuned = {"row_lists": 2, "ticket_origins": 2}
+    assert bench.tube_run_key("batched", 256, (74, 621, 506), tuned) == cap
+    assert bench.tube_run_key("batched", 32, (74, 621, 506), tuned) not in bench.TUBE_DRAM_BYTES
+    assert bench.tube_run_key("batched", 256, (74, 506, 506), tuned) not in bench.TUBE_DRAM_BYTES
+    assert bench.tube_run_key("batched", 256, (74, 621, 506), None, rows=1) not in bench.TUBE_DRAM_BYTES
+    assert bench.tube_run_key("dense", 1, (68, 606, 606), {"row_lists": 2, "ticket_origins": 1})[1:] == \
+        (1, (68, 606, 606), 2, 1)
+    assert bench.hbm_roofline(None, 60.0, {}) is None
+    h = bench.hbm_roofline(6.0e8, 60.0, {"hbm_gbs": 6000.0})
+    assert abs(h["achieved_gbs"] - 10.0) < 1e-9 and abs(h["frac"] - 10.0 / 6000.0) < 1e-12
+    assert h["peak_src"] == "of measured"
+    assert bench.hbm_roofline(6.0e8, 60.0, {})["peak_src"] == "of fallback"
